@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark of the edge-partitioned flux kernel on one GB300.
+
+Workload: the 1M-node mesh (1,048,576 points uniform in the unit cube, seed
+0, symmetrised k=4 nearest-neighbour graph, ~2.57M tasks in shuffled order),
+state x: 5 x fp32 N(0,1), weights w ~ U(0.5, 1.5), explicit steps
+x <- x + 1e-3 * flux(x).  One bench step is one explicit step (edge kernel
+plus shared-vertex update) on the whole mesh, with L2 flushed (a write of
+twice the L2 size) before every timed step and outside its events.
+
+Reported (one JSON line on rank 0):
+  value        forward edge updates/s, partitioned schedule (C = --C)
+  default      the same kernel under the default order (C consecutive tasks)
+  fwd_bwd      10 steps forward + backward (checkpoint every 5, recompute
+               included) through the autograd function, edge updates/s
+  roofline     the forward edge kernel: algorithmic bytes per launch (the cost
+               model of Eq. 1, 4*D bytes per vertex load) / its mean duration
+  e2e          ep_run_host: host x, w in pinned memory, 100 steps, x back
+  cpu_baseline the FP64 oracle on the host, bounded sample of steps
+With --impl reference the oracle itself is timed as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge updates/s, fwd & fwd+bwd, partitioned vs default order; % HBM peak"
+UNIT = "edge updates/s"
+D = 5
+TAU = 1e-3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--C", type=int, default=256)
+    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--n", type=int, default=1 << 20, help="mesh points (default: the 1M-node mesh)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--sweep", action="store_true", help="also time C in {256, 512, 1024}")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(n):
+    import workloads as W
+
+    src, dst = W.knn_mesh(n, 4, 0)
+    x0 = W.flux_state(n, D, 0)
+    w = W.flux_weights(src.size, 0)
+    return src, dst, x0, w
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling while the timed loops run."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def l2_flusher(torch):
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    buf = torch.empty(max(2 * l2, 64 << 20) // 4, dtype=torch.float32, device="cuda")
+    return buf, 2 * l2
+
+
+def timed_loop(torch, body, steps, warmup, flush):
+    """W untimed runs, then `steps` runs each bracketed by events, L2 flushed before each."""
+    for _ in range(warmup):
+        body()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    barrier(torch)
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        body()
+        b.record()
+    torch.cuda.synchronize()
+    barrier(torch)
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def barrier(torch):
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.barrier()
+
+
+def max_over_ranks(torch, value):
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        t = torch.tensor([value], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+    return value
+
+
+def algorithmic_bytes(S, loads, foreign):
+    """Cost-model bytes of one forward edge-kernel launch.
+
+    Task stream (16-bit slot pair + weight, 8 B) + block descriptor (32 B) +
+    foreign record ids (4 B each) + one gather and one write-back of 4*D bytes
+    per vertex load (loads = sum_b |V_b|, Eq. 1)."""
+    return 8 * S.m + 32 * S.k + 4 * foreign + 2 * 4 * D * loads
+
+
+def bench_fwd(torch, E, S, x0, w, steps, warmup, flush):
+    x = torch.from_numpy(x0).cuda()
+    wt = torch.from_numpy(w).cuda()
+    xl = torch.empty(S.layout_floats(D), device="cuda")
+    wl = torch.empty(S.m, device="cuda")
+    S.layout_in(x, xl)
+    S.weights_in(wt, wl)
+    for _ in range(warmup):
+        S.step(D, xl, xl, wl, None, TAU)
+    S.timing(2)
+    ms = timed_loop(torch, lambda: S.step(D, xl, xl, wl, None, TAU), steps, 0, flush)
+    edge_ms, edge_n = S.timing_read(E.T_EDGE_FWD)
+    bnd_ms, bnd_n = S.timing_read(E.T_BND)
+    S.timing(0)
+    return dict(ms=ms, edge_ms=edge_ms / max(edge_n, 1), edge_launches=edge_n,
+                bnd_ms=bnd_ms / max(bnd_n, 1), bnd_launches=bnd_n)
+
+
+def bench_fwd_bwd(torch, S, x0, w, iters, warmup, flush, T=10, every=5):
+    from paper_1605_02043_gb300.autograd import flux_steps
+    import workloads as W
+
+    x = torch.from_numpy(x0).cuda()
+    wt = torch.from_numpy(w).cuda()
+    g = torch.from_numpy(W.loss_weights(S.n, D, 1).astype(np.float32)).cuda()
+
+    def body():
+        xr = x.clone().requires_grad_(True)
+        wr = wt.clone().requires_grad_(True)
+        xT = flux_steps(xr, wr, S, T, TAU, every)
+        xT.backward(g)
+
+    ms = timed_loop(torch, body, iters, warmup, flush)
+    return dict(ms=ms, T=T)
+
+
+def bench_e2e(torch, S, x0, w, reps=3, T=100):
+    xh = torch.from_numpy(x0.copy()).pin_memory()
+    wh = torch.from_numpy(w.copy()).pin_memory()
+    S.run_host(xh, wh, None, steps=T, tau=TAU, D=D)  # warm-up (allocates workspace)
+    barrier(torch)
+    times = []
+    for _ in range(reps):
+        xh.copy_(torch.from_numpy(x0))
+        t0 = time.perf_counter()
+        S.run_host(xh, wh, None, steps=T, tau=TAU, D=D)
+        times.append(time.perf_counter() - t0)
+    t = max_over_ranks(torch, statistics.median(times))
+    return dict(value=S.m * T / t, unit=UNIT, h2d_bytes_per_step=int(xh.numel() * 4 + wh.numel() * 4),
+                d2h_bytes_per_step=int(xh.numel() * 4), steps_per_call=T, seconds_per_call=t)
+
+
+def cpu_baseline(src, dst, x0, w, seconds):
+    import oracle as O
+
+    x = x0.astype(np.float64)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        x, _ = O.flux_steps(src, dst, x, w, 1, TAU)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return dict(value=src.size * steps / el, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{steps} FP64 NumPy flux steps of the full mesh ({src.size} tasks), single thread")
+
+
+def run_reference(args):
+    """The oracle as the reference arm (rank 0 only)."""
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle as O
+
+    src, dst, x0, w = workload(args.n)
+    x = x0.astype(np.float64)
+    for _ in range(max(args.warmup, 3) if args.steps <= 20 else 3):
+        x, _ = O.flux_steps(src, dst, x, w, 1, TAU)
+    # each reference step is one FP64 oracle step on the full mesh; cap the count
+    steps = min(args.steps, 20)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x, _ = O.flux_steps(src, dst, x, w, 1, TAU)
+    el = time.perf_counter() - t0
+    v = src.size * steps / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": 3, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"kNN mesh n={args.n} k=4 (m={src.size}), D=5, explicit flux step",
+                   "C": args.C},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} FP64 NumPy oracle steps of the full mesh"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    import paper_1605_02043_gb300 as E
+
+    src, dst, x0, w = workload(args.n)
+    n, m = args.n, src.size
+    t0 = time.perf_counter()
+    S = E.Schedule.partition(src, dst, n, args.C)
+    part_s = time.perf_counter() - t0
+    Sd = E.Schedule.partition(src, dst, n, args.C, default_order=True)
+    for s in (S, Sd):
+        s.set_threads(args.threads)
+    loads, cut = S.cost()
+    loads_d, cut_d = Sd.cost()
+    assert (loads, cut) == S.cost_host() and (loads_d, cut_d) == Sd.cost_host()
+    flush, flush_bytes = l2_flusher(torch)
+
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    fwd = bench_fwd(torch, E, S, x0, w, args.steps, args.warmup, flush)
+    fwd_d = bench_fwd(torch, E, Sd, x0, w, args.steps, args.warmup, flush)
+    iters = max(3, args.steps // 20)
+    fb = bench_fwd_bwd(torch, S, x0, w, iters, 3, flush)
+    fb_d = bench_fwd_bwd(torch, Sd, x0, w, iters, 3, flush)
+    clk = clocks.stop()
+
+    sweep = {}
+    if args.sweep:
+        for C in (256, 512, 1024):
+            Sc = E.Schedule.partition(src, dst, n, C)
+            Sc.set_threads(args.threads)
+            r = bench_fwd(torch, E, Sc, x0, w, max(10, args.steps // 4), args.warmup, flush)
+            sweep[str(C)] = dict(edge_updates_per_s=m * len(r["ms"]) / (1e-3 * sum(r["ms"])),
+                                 loads=Sc.cost_host()[0])
+
+    e2e = bench_e2e(torch, S, x0, w)
+    tot = max_over_ranks(torch, sum(fwd["ms"]))
+    value = ws * m * len(fwd["ms"]) / (1e-3 * tot)
+    fb_tot = max_over_ranks(torch, sum(fb["ms"]))
+    fb_value = ws * m * fb["T"] * len(fb["ms"]) / (1e-3 * fb_tot)
+
+    # every load beyond a vertex's first block is a foreign record id: sum = vertex cut
+    alg = algorithmic_bytes(S, loads, cut)
+    alg_d = algorithmic_bytes(Sd, loads_d, cut_d)
+    peak, peak_kind = peaks()
+    achieved = alg / (fwd["edge_ms"] * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            tr = json.load(open(tr_path))
+            from paper_1605_02043_gb300 import build as B
+            import hashlib
+            h = hashlib.sha256(open(os.path.join(B.CSRC, "kernels.cu"), "rb").read()).hexdigest()[:16]
+            ent = tr.get(f"flux_fwd_C{args.C}_n{n}")
+            if ent and ent.get("kernels_cu_sha") == h:
+                traffic = ent["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+
+    if rank != 0:
+        return
+    cpu = cpu_baseline(src, dst, x0, w, args.cpu_seconds) if ws == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot / len(fwd["ms"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": f"kNN mesh n={n} k=4 (m={m}), D=5, one explicit flux step per bench step",
+            "schedule": "edge partition (clone-and-connect + recursive bisection)",
+            "C": args.C, "threads_per_block": args.threads, "tau": TAU,
+            "l2": f"flushed before every timed step ({flush_bytes >> 20} MiB write, outside the events)",
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "flux_fwd_kernel<5,8>", "algorithmic_bytes_per_launch": alg,
+                     "launch_ms": fwd["edge_ms"], "peak_kind": f"{peak_kind} HBM copy"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": fwd["edge_launches"] + fwd["bnd_launches"],
+        "clocks": clk,
+        "partitioned": {"edge_updates_per_s": value, "loads": loads, "vertex_cut": cut,
+                        "edge_kernel_ms": fwd["edge_ms"], "bnd_kernel_ms": fwd["bnd_ms"],
+                        "partition_s": part_s, "alg_bytes": alg,
+                        "alg_GBps_edge_kernel": achieved},
+        "default": {"edge_updates_per_s": ws * m * len(fwd_d["ms"]) / (1e-3 * sum(fwd_d["ms"])),
+                    "loads": loads_d, "vertex_cut": cut_d, "edge_kernel_ms": fwd_d["edge_ms"],
+                    "bnd_kernel_ms": fwd_d["bnd_ms"], "alg_bytes": alg_d,
+                    "alg_GBps_edge_kernel": alg_d / (fwd_d["edge_ms"] * 1e-3) / 1e9},
+        "fwd_bwd": {"partitioned": fb_value,
+                    "default": ws * m * fb_d["T"] * len(fb_d["ms"]) / (1e-3 * sum(fb_d["ms"])),
+                    "unit": UNIT, "steps": fb["T"], "checkpoint_every": 5, "iterations": len(fb["ms"])},
+        "C_sweep": sweep or None,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

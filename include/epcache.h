@@ -1,0 +1,221 @@
+/*
+ * epcache.h -- C ABI of libepcache: edge-partitioned gather/interact/scatter
+ * kernels for GB300 (sm_103a).
+ *
+ * Method: "A Graph-based Model for GPU Caching Problems" (Li et al.).  Data
+ * objects are vertices and tasks are edges of a data-affinity graph (Section
+ * 3.1, Definition 1).  Tasks are split into blocks of capacity C so that the
+ * number of distinct vertices each block touches, summed over blocks, is small
+ * (Eq. 1), by the clone-and-connect transform, a balanced vertex partition and
+ * the reconstruction of Definition 4 (Section 3.2).  Each CUDA thread block
+ * then stages its block's distinct vertices in shared memory once (Section 4,
+ * the software-cache kernel) and scatters its results back.
+ *
+ * Conventions for every call:
+ *   - return value 0 (EP_OK) or a negative EP_E* code; ep_last_error() gives
+ *     a message for the calling thread;
+ *   - arrays named "host" are read during the call only and stay owned by the
+ *     caller; device pointers are caller-owned CUDA global memory on the
+ *     current device; the library never frees caller memory;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); device work is enqueued on it and the call returns without
+ *     synchronising unless stated otherwise;
+ *   - a schedule owns its host arrays, its device copy and its device
+ *     workspace.  Calls on one schedule must not overlap in time (they share
+ *     that workspace); distinct schedules are independent.
+ *   - there is no CPU fallback: kernel calls return EP_ENODEV without a CUDA
+ *     device.
+ */
+#ifndef EPCACHE_H
+#define EPCACHE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EP_OK 0
+#define EP_EINVAL (-1)   /* bad argument (sizes, ids out of range, flags) */
+#define EP_ENOMEM (-2)   /* host or device allocation failed */
+#define EP_ECUDA (-3)    /* a CUDA runtime call failed (message has details) */
+#define EP_ETIMEOUT (-4) /* an optimisation thread missed its deadline */
+#define EP_ENODEV (-5)   /* no CUDA device */
+
+/* ep_partition flags */
+#define EP_BIPARTITE 1u     /* SpMV graph: x_j -> vertex j, y_i -> vertex n+i */
+#define EP_DEFAULT_ORDER 2u /* no partitioning: C consecutive tasks per block */
+
+/* kernels */
+#define EP_KERNEL_FLUX 0 /* f = w (x_v - x_u)/(1+|x_v - x_u|^2); out_u += f, out_v -= f */
+#define EP_KERNEL_SPMV 1 /* y_u += w x_v on a bipartite schedule (u = row, v = col) */
+
+#define EP_MAX_D 8       /* state width limit for the flux kernels */
+#define EP_MAX_C 16384   /* block capacity limit (local indices are 16-bit) */
+
+typedef struct ep_schedule ep_schedule; /* opaque, library-owned */
+
+/* Library version (major*10000 + minor*100 + patch). */
+int ep_version(void);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *ep_last_error(void);
+
+/*
+ * Balanced edge partition (Section 3.1 Eq. 1; Section 3.2 Definitions 3-4).
+ *   src, dst  host int32[m]: task e uses data objects src[e] and dst[e],
+ *             both in [0, n).  Task id = position.  Self loops use one object;
+ *             repeated pairs stay separate tasks.  With EP_BIPARTITE the task
+ *             is the nonzero A[src[e]][dst[e]] of an n x n matrix and touches
+ *             x_{dst[e]} (vertex dst[e]) and y_{src[e]} (vertex n + src[e]).
+ *   C         block capacity in tasks, 1 <= C <= EP_MAX_C; k = ceil(m/C)
+ *             blocks, every block holds exactly C tasks except the last.
+ *   flags     EP_BIPARTITE, EP_DEFAULT_ORDER.
+ *   threads   host threads for the recursion (<= 0: all hardware threads).
+ *   out       receives a new schedule; free it with ep_schedule_free().
+ * The result is deterministic and independent of `threads`.  Host-only: runs
+ * without a GPU.  EP_EINVAL for m <= 0, m >= 2^31, n <= 0, ids out of range or
+ * C out of range.
+ */
+int ep_partition(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, int32_t C,
+                 uint32_t flags, int32_t threads, ep_schedule **out);
+
+/* Sizes of a schedule.  nd = number of data vertices (n, or 2n if bipartite).
+ * Any output pointer may be NULL. */
+int ep_schedule_info(const ep_schedule *s, int64_t *m, int64_t *n, int64_t *nd, int64_t *k,
+                     int32_t *C, uint32_t *flags);
+
+/*
+ * Borrowed host views of a schedule (valid until ep_schedule_free):
+ *   block_ptr[k+1]   tasks of block b are edge_perm[block_ptr[b] .. block_ptr[b+1])
+ *   edge_perm[m]     task ids grouped by block, ascending within a block (Def. 4)
+ *   vert_ptr[k+1]    vertices of block b are vert_list[vert_ptr[b] .. vert_ptr[b+1])
+ *   vert_list[L]     distinct vertices per block in first-touch order (task
+ *                    order, endpoint src-side then dst-side); L = loads
+ *   relabel[nd]      cpack id of every data vertex (Section 4.1): order of first
+ *                    appearance over blocks 0..k-1, untouched vertices last
+ * Any output pointer may be NULL.
+ */
+int ep_schedule_arrays(const ep_schedule *s, const int64_t **block_ptr, const int32_t **edge_perm,
+                       const int64_t **vert_ptr, const int32_t **vert_list,
+                       const int32_t **relabel);
+
+/* Host-side cost (Eq. 1): loads = sum_b |V_b|, vertex_cut = sum_v (p_v - 1). */
+int ep_cost_host(const ep_schedule *s, int64_t *loads, int64_t *vertex_cut);
+
+/*
+ * GPU cost (Section 3.1, Definition 2 and Eq. 1): one CUDA block per schedule
+ * block sorts that block's 2|block| endpoint ids in shared memory, counts the
+ * distinct ones and marks touched vertices; loads = sum_b |V_b| and
+ * vertex_cut = loads - #touched.  Uploads the schedule on first use.
+ * Synchronises `stream` (the results are host values).
+ */
+int ep_cost(ep_schedule *s, int64_t *loads, int64_t *vertex_cut, void *stream);
+
+/*
+ * Forward run in the caller's layout (device pointers):
+ *   EP_KERNEL_FLUX: x float[D][n] (in: x_0, out: x_T), w float[m] (task
+ *     order), out float[D][n] or NULL (receives flux(x_{T-1})), 1 <= D <=
+ *     EP_MAX_D, steps = T >= 1 explicit steps x_{t+1} = x_t + tau*flux(x_t).
+ *     With tau = 0, x is unchanged and out = flux(x).
+ *   EP_KERNEL_SPMV (bipartite schedule): x float[n] (read), w float[m],
+ *     out float[n] = y (written), D = 1, steps = 1, tau ignored.
+ * Uses schedule-owned device workspace (allocated on first use: make the
+ * first call before any stream capture).
+ */
+int ep_run(ep_schedule *s, int32_t kernel, float *x, const float *w, float *out, int32_t D,
+           int32_t steps, float tau, void *stream);
+
+/*
+ * Same as ep_run with HOST pointers (x in/out, w in, out optional): copies
+ * inputs to the device, runs, copies results back and synchronises.
+ */
+int ep_run_host(ep_schedule *s, int32_t kernel, float *x, const float *w, float *out, int32_t D,
+                int32_t steps, float tau, void *stream);
+
+/*
+ * Reverse sweep of `steps` flux steps started from x0 (device, float[D][n],
+ * caller layout): recomputes x_0..x_{T-1} into workspace, then for t = T-1..0
+ *   gbar_e = lam_u - lam_v, d = x_v - x_u, s = |d|^2,
+ *   grad_w[e] += tau <gbar_e, d>/(1+s),
+ *   lam += tau * scatter(+h_e to v, -h_e to u),
+ *   h_e = w_e (gbar_e/(1+s) - 2 d (d.gbar_e)/(1+s)^2).
+ * lam float[D][n]: in dL/dx_T, out dL/dx_0.  grad_w float[m]: accumulated.
+ */
+int ep_run_adjoint(ep_schedule *s, const float *x0, const float *w, float *lam, float *grad_w,
+                   int32_t D, int32_t steps, float tau, void *stream);
+
+/* ----------------------------------------------------- schedule layout API
+ * The kernels work on the schedule's own layout (the paper's opt_arrayA):
+ * every touched vertex is a record of R = ep_record_floats(D) floats
+ * (R = 1, 2, 4 or 8 >= D, padding lanes zero), ordered by cpack with the
+ * vertices used by one block only placed first.  Tasks are in edge_perm order.
+ * Keeping state in this layout across calls avoids the permutations.
+ */
+int32_t ep_record_floats(int32_t D);
+/* Floats needed for one state buffer in schedule layout (n_records * R). */
+int64_t ep_layout_floats(const ep_schedule *s, int32_t D);
+/* x_lay <- x (caller layout float[D][n]); padding lanes zeroed. */
+int ep_layout_in(ep_schedule *s, int32_t D, const float *x, float *x_lay, void *stream);
+/* x <- x_lay (caller layout float[D][n]). */
+int ep_layout_out(ep_schedule *s, int32_t D, const float *x_lay, float *x, void *stream);
+/* w_lay[i] <- w[edge_perm[i]]. */
+int ep_weights_in(ep_schedule *s, const float *w, float *w_lay, void *stream);
+/* w[edge_perm[i]] += w_lay[i]. */
+int ep_weights_out_add(ep_schedule *s, const float *w_lay, float *w, void *stream);
+
+/*
+ * One explicit flux step in schedule layout: x_out = x_in + tau*flux(x_in)
+ * (x_out may equal x_in), out_lay = flux(x_in) if not NULL.  Two kernel
+ * launches; uses schedule-owned boundary accumulators (zero between calls).
+ */
+int ep_step(ep_schedule *s, int32_t D, const float *x_in, float *x_out, const float *w_lay,
+            float *out_lay, float tau, void *stream);
+
+/*
+ * One adjoint step in schedule layout: lam (in lam_{t+1}, out lam_t) and
+ * grad_w_lay += per-task terms, evaluated at state x_lay = x_t.
+ */
+int ep_adjoint_step(ep_schedule *s, int32_t D, const float *x_lay, const float *w_lay, float *lam,
+                    float *grad_w_lay, float tau, void *stream);
+
+/*
+ * Merge independent schedules (disjoint graphs, e.g. many meshes) into one
+ * schedule whose blocks run in a single launch.  Vertex ids of part i are
+ * offset by the sum of the n of parts 0..i-1, task ids likewise by m.  The
+ * parts must share flags and may differ in C.  The parts stay valid.
+ */
+int ep_batch(ep_schedule *const *parts, int32_t count, ep_schedule **out);
+
+/*
+ * Per-kernel timing (instrumentation, off by default).  When enabled, every
+ * launch of the schedule's kernels is bracketed by CUDA events recorded on
+ * its own stream; ep_timing_read() waits for the recorded events and returns
+ * the summed device time and launch count of one kernel class since the last
+ * reset:
+ *   EP_T_EDGE_FWD  flux edge kernel (forward)      EP_T_BND   shared-vertex update
+ *   EP_T_EDGE_ADJ  flux edge kernel (adjoint)      EP_T_SPMV  SpMV edge kernel
+ *   EP_T_LAYOUT    layout / weight permutations    EP_T_COST  cost kernels
+ * enable = 0 turns timing off; enable = 2 clears the totals and keeps it on.
+ */
+#define EP_T_EDGE_FWD 0
+#define EP_T_BND 1
+#define EP_T_EDGE_ADJ 2
+#define EP_T_SPMV 3
+#define EP_T_LAYOUT 4
+#define EP_T_COST 5
+#define EP_T_CLASSES 6
+int ep_timing(ep_schedule *s, int32_t enable);
+int ep_timing_read(ep_schedule *s, int32_t kernel_class, double *total_ms, int64_t *launches);
+
+/* Threads per CUDA block of the edge kernels (32..1024, multiple of 32;
+ * default 256).  Does not change results beyond FP32 rounding order. */
+int ep_set_threads(ep_schedule *s, int32_t threads);
+
+void ep_schedule_free(ep_schedule *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPCACHE_H */

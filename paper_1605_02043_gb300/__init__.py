@@ -1,0 +1,214 @@
+"""Edge-partitioned gather/interact/scatter kernels on GB300.
+
+Python face of libepcache (include/epcache.h).  Every call is argument
+marshalling into the C ABI: the partition runs in the library's C++ host code,
+every per-task and per-vertex computation runs in its CUDA kernels.  There is
+no CPU fallback; kernel calls raise when no CUDA device or library is there.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import EpError, check, lib
+
+__all__ = ["Schedule", "EpError", "FLUX", "SPMV", "BIPARTITE", "DEFAULT_ORDER", "record_floats",
+           "T_EDGE_FWD", "T_BND", "T_EDGE_ADJ", "T_SPMV", "T_LAYOUT", "T_COST"]
+
+FLUX = 0
+SPMV = 1
+BIPARTITE = 1
+DEFAULT_ORDER = 2
+# kernel classes of Schedule.timing_read (EP_T_* in epcache.h)
+T_EDGE_FWD, T_BND, T_EDGE_ADJ, T_SPMV, T_LAYOUT, T_COST = range(6)
+
+
+def _vp(t):
+    """Device pointer of a tensor (or None)."""
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need_cuda_f32(t, name, numel=None):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+
+
+def record_floats(D: int) -> int:
+    return int(lib().ep_record_floats(D))
+
+
+class Schedule:
+    """A partitioned task schedule (owns host arrays, device copy, workspace)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        m, n, nd, k = (ctypes.c_int64() for _ in range(4))
+        C = ctypes.c_int32()
+        fl = ctypes.c_uint32()
+        check(lib().ep_schedule_info(self._h, *(ctypes.byref(v) for v in (m, n, nd, k, C, fl))))
+        self.m, self.n, self.nd, self.k = m.value, n.value, nd.value, k.value
+        self.C, self.flags = C.value, fl.value
+
+    # ---------------------------------------------------------------- build
+    @classmethod
+    def partition(cls, src, dst, n: int, C: int, bipartite: bool = False,
+                  default_order: bool = False, threads: int = 0) -> "Schedule":
+        src = np.ascontiguousarray(src, np.int32)
+        dst = np.ascontiguousarray(dst, np.int32)
+        if src.shape != dst.shape or src.ndim != 1:
+            raise ValueError("src and dst must be equal-length 1-D arrays")
+        flags = (BIPARTITE if bipartite else 0) | (DEFAULT_ORDER if default_order else 0)
+        h = ctypes.c_void_p()
+        check(lib().ep_partition(src.ctypes.data, dst.ctypes.data, src.size, n, C, flags, threads,
+                                 ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def batch(cls, parts) -> "Schedule":
+        arr = (ctypes.c_void_p * len(parts))(*[p._h for p in parts])
+        h = ctypes.c_void_p()
+        check(lib().ep_batch(arr, len(parts), ctypes.byref(h)))
+        return cls(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ep_schedule_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def bipartite(self) -> bool:
+        return bool(self.flags & BIPARTITE)
+
+    # ---------------------------------------------------------------- views
+    def arrays(self) -> dict:
+        """Copies of the schedule's host arrays (see ep_schedule_arrays)."""
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        check(lib().ep_schedule_arrays(self._h, *(ctypes.byref(p) for p in ptrs)))
+        loads, cut = self.cost_host()
+
+        def view(p, ctype, count, dtype):
+            if count == 0:
+                return np.zeros(0, dtype)
+            buf = (ctype * count).from_address(p.value)
+            return np.frombuffer(buf, dtype=dtype).copy()
+
+        return dict(
+            k=self.k,
+            block_ptr=view(ptrs[0], ctypes.c_int64, self.k + 1, np.int64),
+            edge_perm=view(ptrs[1], ctypes.c_int32, self.m, np.int32),
+            vert_ptr=view(ptrs[2], ctypes.c_int64, self.k + 1, np.int64),
+            vert_list=view(ptrs[3], ctypes.c_int32, loads, np.int32),
+            relabel=view(ptrs[4], ctypes.c_int32, self.nd, np.int32),
+            loads=loads, cut=cut,
+        )
+
+    def part(self) -> np.ndarray:
+        """Block id of every task."""
+        a = self.arrays()
+        p = np.empty(self.m, np.int32)
+        for b in range(self.k):
+            p[a["edge_perm"][a["block_ptr"][b]:a["block_ptr"][b + 1]]] = b
+        return p
+
+    def cost_host(self):
+        loads, cut = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().ep_cost_host(self._h, ctypes.byref(loads), ctypes.byref(cut)))
+        return loads.value, cut.value
+
+    def cost(self, stream=None):
+        """(loads, vertex cut) computed by the GPU sort/unique kernel."""
+        loads, cut = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().ep_cost(self._h, ctypes.byref(loads), ctypes.byref(cut), _stream(stream)))
+        return loads.value, cut.value
+
+    # ------------------------------------------------------------- kernels
+    def run(self, x, w, out=None, steps: int = 1, tau: float = 1e-3, kernel: int = FLUX,
+            stream=None):
+        """Forward run in the caller's layout (see ep_run); x is updated in place."""
+        D = 1 if kernel == SPMV else int(x.shape[0])
+        nx = self.n if kernel == SPMV else D * self.n
+        _need_cuda_f32(x, "x", nx)
+        _need_cuda_f32(w, "w", self.m)
+        if out is not None:
+            _need_cuda_f32(out, "out", nx)
+        check(lib().ep_run(self._h, kernel, _vp(x), _vp(w), _vp(out), D, steps, tau, _stream(stream)))
+        return x if kernel == FLUX else out
+
+    def run_host(self, x, w, out=None, steps: int = 1, tau: float = 1e-3, kernel: int = FLUX,
+                 D: int = 1, stream=None):
+        """ep_run_host on host tensors/arrays (pinned memory recommended)."""
+        def ptr(a):
+            if a is None:
+                return None
+            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+        check(lib().ep_run_host(self._h, kernel, ptr(x), ptr(w), ptr(out), D, steps, tau,
+                                _stream(stream)))
+
+    def run_adjoint(self, x0, w, lam, grad_w, steps: int, tau: float = 1e-3, stream=None):
+        D = int(x0.shape[0])
+        for t, nm, k in ((x0, "x0", D * self.n), (lam, "lam", D * self.n), (w, "w", self.m),
+                         (grad_w, "grad_w", self.m)):
+            _need_cuda_f32(t, nm, k)
+        check(lib().ep_run_adjoint(self._h, _vp(x0), _vp(w), _vp(lam), _vp(grad_w), D, steps, tau,
+                                   _stream(stream)))
+
+    # ------------------------------------------------------------ tuning
+    def set_threads(self, threads: int):
+        check(lib().ep_set_threads(self._h, threads))
+
+    def timing(self, enable: int = 2):
+        """Start (2 = clear and start), keep (1) or stop (0) per-kernel timing."""
+        check(lib().ep_timing(self._h, enable))
+
+    def timing_read(self, kernel_class: int):
+        """(total ms, launches) of one kernel class since the last clear."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        check(lib().ep_timing_read(self._h, kernel_class, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    # ------------------------------------------------------ schedule layout
+    def layout_floats(self, D: int) -> int:
+        return int(lib().ep_layout_floats(self._h, D))
+
+    def layout_in(self, x, x_lay, stream=None):
+        check(lib().ep_layout_in(self._h, int(x.shape[0]), _vp(x), _vp(x_lay), _stream(stream)))
+
+    def layout_out(self, x_lay, x, stream=None):
+        check(lib().ep_layout_out(self._h, int(x.shape[0]), _vp(x_lay), _vp(x), _stream(stream)))
+
+    def weights_in(self, w, w_lay, stream=None):
+        check(lib().ep_weights_in(self._h, _vp(w), _vp(w_lay), _stream(stream)))
+
+    def weights_out_add(self, w_lay, w, stream=None):
+        check(lib().ep_weights_out_add(self._h, _vp(w_lay), _vp(w), _stream(stream)))
+
+    def step(self, D: int, x_in, x_out, w_lay, out_lay=None, tau: float = 1e-3, stream=None):
+        check(lib().ep_step(self._h, D, _vp(x_in), _vp(x_out), _vp(w_lay), _vp(out_lay), tau,
+                            _stream(stream)))
+
+    def adjoint_step(self, D: int, x_lay, w_lay, lam, grad_w_lay, tau: float = 1e-3, stream=None):
+        check(lib().ep_adjoint_step(self._h, D, _vp(x_lay), _vp(w_lay), _vp(lam), _vp(grad_w_lay),
+                                    tau, _stream(stream)))

@@ -1,0 +1,622 @@
+// capi.cu -- the extern "C" boundary of libepcache (declared in epcache.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+
+#include "../../include/epcache.h"
+#include "internal.h"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_error = buf;
+  return code;
+}
+
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (b <= bytes && p) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, b ? b : 16);
+    if (e == cudaSuccess) bytes = b ? b : 16;
+    return e;
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+template <typename T>
+cudaError_t upload(DBuf& d, const std::vector<T>& v) {
+  cudaError_t e = d.ensure(v.size() * sizeof(T));
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpy(d.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Event pairs recorded around launches; resolved lazily in ep_timing_read.
+struct EventTimer final : ep::dev::Timer {
+  bool on = false;
+  struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t open = nullptr;
+  double total[EP_T_CLASSES] = {};
+  int64_t count[EP_T_CLASSES] = {};
+
+  cudaEvent_t take() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  void begin(int, cudaStream_t st) override {
+    if (!on) return;
+    open = take();
+    if (open) cudaEventRecord(open, st);
+  }
+  void end(int cls, cudaStream_t st) override {
+    if (!on || !open) return;
+    cudaEvent_t e = take();
+    if (!e) return;
+    cudaEventRecord(e, st);
+    pending.push_back({cls, open, e});
+    open = nullptr;
+    if (pending.size() > 8192) collect();
+  }
+  void collect() {
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        total[p.cls] += ms;
+        count[p.cls] += 1;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void clear() {
+    collect();
+    for (int i = 0; i < EP_T_CLASSES; ++i) {
+      total[i] = 0;
+      count[i] = 0;
+    }
+  }
+  ~EventTimer() override {
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+}  // namespace
+
+struct ep_schedule {
+  ep::HostSchedule h;
+  int device = -1;  // device holding the uploaded copy, -1 before upload
+  int tpb = 256;
+  bool bacc_dirty = true;
+  // device copy of the schedule
+  DBuf d_desc, d_flist, d_ylist, d_loc, d_perm, d_rec, d_xrec, d_yrec, d_bptr, d_eu, d_ev;
+  // workspace
+  DBuf ws_x, ws_out, ws_w, ws_bacc, ws_lam, ws_gw, ws_hist, ws_flags, ws_cnt;
+  DBuf ws_hx, ws_hw, ws_hout;
+  EventTimer timer;
+  ep::dev::Timer* t() { return timer.on ? &timer : nullptr; }
+};
+
+namespace {
+
+bool bipartite(const ep_schedule* s) { return (s->h.flags & EP_BIPARTITE) != 0; }
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      s->bacc_dirty = true;                                                               \
+      return fail(EP_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    }                                                                                     \
+  } while (0)
+
+// Makes sure a CUDA device exists and the schedule is uploaded to the current one.
+int ensure_device(ep_schedule* s) {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    return fail(EP_ENODEV, "no CUDA device");
+  }
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (s->device >= 0) {
+    if (dev != s->device)
+      return fail(EP_EINVAL, "schedule lives on device %d, current device is %d", s->device, dev);
+    return EP_OK;
+  }
+  const ep::HostSchedule& h = s->h;
+  std::vector<int32_t> eu(h.m), ev(h.m);
+  for (int64_t i = 0; i < h.m; ++i) {
+    const int32_t e = h.edge_perm[i];
+    eu[i] = bipartite(s) ? (int32_t)(h.n + h.src[e]) : h.src[e];
+    ev[i] = h.dst[e];
+  }
+  CU(upload(s->d_eu, eu));
+  CU(upload(s->d_ev, ev));
+  CU(upload(s->d_bptr, h.block_ptr));
+  CU(upload(s->d_perm, h.edge_perm));
+  CU(upload(s->d_loc, h.loc));
+  if (bipartite(s)) {
+    CU(upload(s->d_desc, h.sdesc));
+    CU(upload(s->d_flist, h.xlist));
+    CU(upload(s->d_ylist, h.ylist));
+    CU(upload(s->d_xrec, h.xrec_of));
+    CU(upload(s->d_yrec, h.yrec_of));
+  } else {
+    CU(upload(s->d_desc, h.fdesc));
+    CU(upload(s->d_flist, h.flist));
+    CU(upload(s->d_rec, h.rec_of));
+  }
+  s->device = dev;
+  return EP_OK;
+}
+
+cudaStream_t as_stream(void* p) { return static_cast<cudaStream_t>(p); }
+
+ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, float* x_out,
+                            float* out, float tau) {
+  ep::dev::FluxArgs a;
+  a.desc = s->d_desc.as<ep::FluxDesc>();
+  a.k = s->h.k;
+  a.flist = s->d_flist.as<int32_t>();
+  a.loc = s->d_loc.as<uint32_t>();
+  a.w = w;
+  a.x_in = x_in;
+  a.x_out = x_out;
+  a.bacc = s->ws_bacc.as<float>();
+  a.out = out;
+  a.n_int = s->h.n_int;
+  a.n_bnd = s->h.n_bnd;
+  a.tau = tau;
+  a.max_nv = s->h.max_nv;
+  a.tpb = s->tpb;
+  a.timer = s->t();
+  return a;
+}
+
+// boundary accumulators: allocated, zero
+int ensure_bacc(ep_schedule* s, int32_t R, cudaStream_t st) {
+  const size_t bytes = (size_t)s->h.n_bnd * R * sizeof(float);
+  if (s->ws_bacc.bytes < bytes || !s->ws_bacc.p) {
+    CU(s->ws_bacc.ensure(bytes));
+    s->bacc_dirty = true;
+  }
+  if (s->bacc_dirty) {
+    CU(cudaMemsetAsync(s->ws_bacc.p, 0, s->ws_bacc.bytes, st));
+    s->bacc_dirty = false;
+  }
+  return EP_OK;
+}
+
+int check_flux(ep_schedule* s, int32_t D) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (bipartite(s)) return fail(EP_EINVAL, "flux kernels need a non-bipartite schedule");
+  if (D < 1 || D > EP_MAX_D) return fail(EP_EINVAL, "D = %d out of [1, %d]", D, EP_MAX_D);
+  return EP_OK;
+}
+
+int run_spmv(ep_schedule* s, const float* x, const float* w, float* y, cudaStream_t st) {
+  const ep::HostSchedule& h = s->h;
+  CU(s->ws_x.ensure((size_t)h.n * sizeof(float)));
+  CU(s->ws_out.ensure((size_t)h.n * sizeof(float)));
+  CU(s->ws_w.ensure((size_t)h.m * sizeof(float)));
+  CU(ep::dev::layout_in(s->d_xrec.as<int32_t>(), h.n, 1, 1, x, s->ws_x.as<float>(), st, s->t()));
+  CU(ep::dev::gather(s->d_perm.as<int32_t>(), h.m, w, s->ws_w.as<float>(), st, s->t()));
+  ep::dev::SpmvArgs a;
+  a.desc = s->d_desc.as<ep::SpmvDesc>();
+  a.k = h.k;
+  a.xlist = s->d_flist.as<int32_t>();
+  a.ylist = s->d_ylist.as<int32_t>();
+  a.loc = s->d_loc.as<uint32_t>();
+  a.w = s->ws_w.as<float>();
+  a.x = s->ws_x.as<float>();
+  a.y = s->ws_out.as<float>();
+  a.ny_int = h.ny_int;
+  a.ny_zero = h.n - h.ny_int;
+  a.max_nx = h.max_nx;
+  a.max_ny = h.max_ny;
+  a.tpb = s->tpb;
+  a.timer = s->t();
+  CU(ep::dev::spmv(a, st));
+  CU(ep::dev::layout_out(s->d_yrec.as<int32_t>(), h.n, 1, 1, s->ws_out.as<float>(), y, st, s->t()));
+  return EP_OK;
+}
+
+int new_schedule(ep_schedule** out, ep_schedule** holder) {
+  ep_schedule* s = new (std::nothrow) ep_schedule();
+  if (!s) return fail(EP_ENOMEM, "out of host memory");
+  *holder = s;
+  (void)out;
+  return EP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ep_version(void) { return 100; }
+
+const char* ep_last_error(void) { return g_error.c_str(); }
+
+int ep_partition(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t C,
+                 uint32_t flags, int32_t threads, ep_schedule** out) {
+  g_error.clear();
+  if (!out) return fail(EP_EINVAL, "null output pointer");
+  *out = nullptr;
+  if (!src || !dst) return fail(EP_EINVAL, "null edge arrays");
+  if (m <= 0 || m >= INT32_MAX) return fail(EP_EINVAL, "m = %lld out of range", (long long)m);
+  if (n <= 0 || n >= INT32_MAX / 2) return fail(EP_EINVAL, "n = %lld out of range", (long long)n);
+  if (C < 1 || C > EP_MAX_C) return fail(EP_EINVAL, "C = %d out of [1, %d]", C, EP_MAX_C);
+  if (flags & ~(EP_BIPARTITE | EP_DEFAULT_ORDER)) return fail(EP_EINVAL, "unknown flags");
+  for (int64_t e = 0; e < m; ++e)
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
+      return fail(EP_EINVAL, "task %lld uses a vertex outside [0, %lld)", (long long)e, (long long)n);
+  ep_schedule* s = nullptr;
+  if (int rc = new_schedule(out, &s)) return rc;
+  try {
+    ep::HostSchedule& h = s->h;
+    h.m = m;
+    h.n = n;
+    h.nd = (flags & EP_BIPARTITE) ? 2 * n : n;
+    h.C = C;
+    h.flags = flags;
+    h.k = (m + C - 1) / C;
+    h.src.assign(src, src + m);
+    h.dst.assign(dst, dst + m);
+    h.part.resize(m);
+    ep::partition_edges(src, dst, m, n, C, flags, threads, h.part.data());
+    std::string err = ep::build_schedule(h, threads);
+    if (!err.empty()) {
+      delete s;
+      return fail(EP_EINVAL, "%s", err.c_str());
+    }
+  } catch (const std::bad_alloc&) {
+    delete s;
+    return fail(EP_ENOMEM, "out of host memory");
+  }
+  *out = s;
+  return EP_OK;
+}
+
+int ep_batch(ep_schedule* const* parts, int32_t count, ep_schedule** out) {
+  g_error.clear();
+  if (!out || !parts || count <= 0) return fail(EP_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  int64_t m = 0, n = 0, k = 0;
+  int32_t C = 0;
+  const uint32_t flags = parts[0] ? parts[0]->h.flags : 0;
+  for (int32_t i = 0; i < count; ++i) {
+    if (!parts[i]) return fail(EP_EINVAL, "null part %d", i);
+    if (parts[i]->h.flags != flags) return fail(EP_EINVAL, "parts differ in flags");
+    m += parts[i]->h.m;
+    n += parts[i]->h.n;
+    k += parts[i]->h.k;
+    C = std::max(C, parts[i]->h.C);
+  }
+  if (m >= INT32_MAX || n >= INT32_MAX / 2) return fail(EP_EINVAL, "batch too large");
+  ep_schedule* s = nullptr;
+  if (int rc = new_schedule(out, &s)) return rc;
+  try {
+    ep::HostSchedule& h = s->h;
+    h.m = m;
+    h.n = n;
+    h.nd = (flags & EP_BIPARTITE) ? 2 * n : n;
+    h.C = C;
+    h.flags = flags & ~EP_DEFAULT_ORDER;
+    h.k = k;
+    h.src.reserve(m);
+    h.dst.reserve(m);
+    h.part.reserve(m);
+    int64_t voff = 0, boff = 0;
+    for (int32_t i = 0; i < count; ++i) {
+      const ep::HostSchedule& p = parts[i]->h;
+      for (int64_t e = 0; e < p.m; ++e) {
+        h.src.push_back((int32_t)(p.src[e] + voff));
+        h.dst.push_back((int32_t)(p.dst[e] + voff));
+        h.part.push_back((int32_t)(p.part[e] + boff));
+      }
+      voff += p.n;
+      boff += p.k;
+    }
+    std::string err = ep::build_schedule(h, 0);
+    if (!err.empty()) {
+      delete s;
+      return fail(EP_EINVAL, "%s", err.c_str());
+    }
+  } catch (const std::bad_alloc&) {
+    delete s;
+    return fail(EP_ENOMEM, "out of host memory");
+  }
+  *out = s;
+  return EP_OK;
+}
+
+void ep_schedule_free(ep_schedule* s) { delete s; }
+
+int ep_schedule_info(const ep_schedule* s, int64_t* m, int64_t* n, int64_t* nd, int64_t* k,
+                     int32_t* C, uint32_t* flags) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (m) *m = s->h.m;
+  if (n) *n = s->h.n;
+  if (nd) *nd = s->h.nd;
+  if (k) *k = s->h.k;
+  if (C) *C = s->h.C;
+  if (flags) *flags = s->h.flags;
+  return EP_OK;
+}
+
+int ep_schedule_arrays(const ep_schedule* s, const int64_t** block_ptr, const int32_t** edge_perm,
+                       const int64_t** vert_ptr, const int32_t** vert_list, const int32_t** relabel) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (block_ptr) *block_ptr = s->h.block_ptr.data();
+  if (edge_perm) *edge_perm = s->h.edge_perm.data();
+  if (vert_ptr) *vert_ptr = s->h.vert_ptr.data();
+  if (vert_list) *vert_list = s->h.vert_list.data();
+  if (relabel) *relabel = s->h.relabel.data();
+  return EP_OK;
+}
+
+int ep_cost_host(const ep_schedule* s, int64_t* loads, int64_t* vertex_cut) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (loads) *loads = s->h.loads;
+  if (vertex_cut) *vertex_cut = s->h.loads - s->h.touched;
+  return EP_OK;
+}
+
+int ep_cost(ep_schedule* s, int64_t* loads, int64_t* vertex_cut, void* stream) {
+  g_error.clear();
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (int rc = ensure_device(s)) return rc;
+  cudaStream_t st = as_stream(stream);
+  CU(s->ws_flags.ensure((size_t)s->h.nd));
+  CU(s->ws_cnt.ensure(2 * sizeof(unsigned long long)));
+  ep::dev::CostArgs a;
+  a.block_ptr = s->d_bptr.as<int64_t>();
+  a.k = s->h.k;
+  a.eu = s->d_eu.as<int32_t>();
+  a.ev = s->d_ev.as<int32_t>();
+  a.max_ne = s->h.max_ne;
+  a.touched = s->ws_flags.as<uint8_t>();
+  a.nd = s->h.nd;
+  a.counters = s->ws_cnt.as<unsigned long long>();
+  a.timer = s->t();
+  CU(ep::dev::cost(a, st));
+  unsigned long long c[2];
+  CU(cudaMemcpyAsync(c, a.counters, sizeof c, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (loads) *loads = (int64_t)c[0];
+  if (vertex_cut) *vertex_cut = (int64_t)c[0] - (int64_t)c[1];
+  return EP_OK;
+}
+
+int32_t ep_record_floats(int32_t D) { return ep::record_floats(D); }
+
+int64_t ep_layout_floats(const ep_schedule* s, int32_t D) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  return bipartite(s) ? s->h.n : s->h.nd * ep::record_floats(D);
+}
+
+int ep_layout_in(ep_schedule* s, int32_t D, const float* x, float* x_lay, void* stream) {
+  g_error.clear();
+  if (int rc = check_flux(s, D)) return rc;
+  if (int rc = ensure_device(s)) return rc;
+  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), s->h.nd, D, ep::record_floats(D), x, x_lay,
+                        as_stream(stream), s->t()));
+  return EP_OK;
+}
+
+int ep_layout_out(ep_schedule* s, int32_t D, const float* x_lay, float* x, void* stream) {
+  g_error.clear();
+  if (int rc = check_flux(s, D)) return rc;
+  if (int rc = ensure_device(s)) return rc;
+  CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), s->h.nd, D, ep::record_floats(D), x_lay, x,
+                         as_stream(stream), s->t()));
+  return EP_OK;
+}
+
+int ep_weights_in(ep_schedule* s, const float* w, float* w_lay, void* stream) {
+  g_error.clear();
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (int rc = ensure_device(s)) return rc;
+  CU(ep::dev::gather(s->d_perm.as<int32_t>(), s->h.m, w, w_lay, as_stream(stream), s->t()));
+  return EP_OK;
+}
+
+int ep_weights_out_add(ep_schedule* s, const float* w_lay, float* w, void* stream) {
+  g_error.clear();
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (int rc = ensure_device(s)) return rc;
+  CU(ep::dev::scatter_add(s->d_perm.as<int32_t>(), s->h.m, w_lay, w, as_stream(stream), s->t()));
+  return EP_OK;
+}
+
+int ep_step(ep_schedule* s, int32_t D, const float* x_in, float* x_out, const float* w_lay,
+            float* out_lay, float tau, void* stream) {
+  g_error.clear();
+  if (int rc = check_flux(s, D)) return rc;
+  if (int rc = ensure_device(s)) return rc;
+  cudaStream_t st = as_stream(stream);
+  const int32_t R = ep::record_floats(D);
+  if (int rc = ensure_bacc(s, R, st)) return rc;
+  if (out_lay && s->h.nd > s->h.n_int + s->h.n_bnd) {
+    const int64_t t = s->h.n_int + s->h.n_bnd;
+    CU(cudaMemsetAsync(out_lay + t * R, 0, (size_t)(s->h.nd - t) * R * sizeof(float), st));
+  }
+  CU(ep::dev::flux_step(flux_args(s, w_lay, x_in, x_out, out_lay, tau), D, st));
+  return EP_OK;
+}
+
+int ep_adjoint_step(ep_schedule* s, int32_t D, const float* x_lay, const float* w_lay, float* lam,
+                    float* grad_w_lay, float tau, void* stream) {
+  g_error.clear();
+  if (int rc = check_flux(s, D)) return rc;
+  if (int rc = ensure_device(s)) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (int rc = ensure_bacc(s, ep::record_floats(D), st)) return rc;
+  CU(ep::dev::flux_adjoint_step(flux_args(s, w_lay, x_lay, nullptr, nullptr, tau), D, lam,
+                                grad_w_lay, st));
+  return EP_OK;
+}
+
+int ep_run(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out, int32_t D,
+           int32_t steps, float tau, void* stream) {
+  g_error.clear();
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (!x || !w) return fail(EP_EINVAL, "null x or w");
+  cudaStream_t st = as_stream(stream);
+  if (kernel == EP_KERNEL_SPMV) {
+    if (!bipartite(s)) return fail(EP_EINVAL, "SpMV needs a bipartite schedule");
+    if (D != 1 || steps != 1) return fail(EP_EINVAL, "SpMV takes D = 1 and steps = 1");
+    if (!out) return fail(EP_EINVAL, "SpMV needs an output vector");
+    if (int rc = ensure_device(s)) return rc;
+    return run_spmv(s, x, w, out, st);
+  }
+  if (kernel != EP_KERNEL_FLUX) return fail(EP_EINVAL, "unknown kernel %d", kernel);
+  if (int rc = check_flux(s, D)) return rc;
+  if (steps < 1) return fail(EP_EINVAL, "steps must be >= 1");
+  if (int rc = ensure_device(s)) return rc;
+  const ep::HostSchedule& h = s->h;
+  const int32_t R = ep::record_floats(D);
+  const size_t lay = (size_t)h.nd * R * sizeof(float);
+  CU(s->ws_x.ensure(lay));
+  CU(s->ws_w.ensure((size_t)h.m * sizeof(float)));
+  if (out) {
+    CU(s->ws_out.ensure(lay));
+  }
+  if (int rc = ensure_bacc(s, R, st)) return rc;
+  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, D, R, x, s->ws_x.as<float>(), st, s->t()));
+  CU(ep::dev::gather(s->d_perm.as<int32_t>(), h.m, w, s->ws_w.as<float>(), st, s->t()));
+  if (out) CU(cudaMemsetAsync(s->ws_out.p, 0, lay, st));
+  for (int32_t t = 0; t < steps; ++t) {
+    float* o = (out && t == steps - 1) ? s->ws_out.as<float>() : nullptr;
+    CU(ep::dev::flux_step(flux_args(s, s->ws_w.as<float>(), s->ws_x.as<float>(),
+                                    s->ws_x.as<float>(), o, tau),
+                          D, st));
+  }
+  CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, D, R, s->ws_x.as<float>(), x, st, s->t()));
+  if (out) CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, D, R, s->ws_out.as<float>(), out, st, s->t()));
+  return EP_OK;
+}
+
+int ep_run_host(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out, int32_t D,
+                int32_t steps, float tau, void* stream) {
+  g_error.clear();
+  if (!s || !x || !w) return fail(EP_EINVAL, "null argument");
+  if (D < 1 || D > EP_MAX_D) return fail(EP_EINVAL, "D out of range");
+  if (int rc = ensure_device(s)) return rc;
+  cudaStream_t st = as_stream(stream);
+  const ep::HostSchedule& h = s->h;
+  const size_t xb = (size_t)(kernel == EP_KERNEL_SPMV ? h.n : h.n * D) * sizeof(float);
+  CU(s->ws_hx.ensure(xb));
+  CU(s->ws_hw.ensure((size_t)h.m * sizeof(float)));
+  if (out) CU(s->ws_hout.ensure(xb));
+  CU(cudaMemcpyAsync(s->ws_hx.p, x, xb, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(s->ws_hw.p, w, (size_t)h.m * sizeof(float), cudaMemcpyHostToDevice, st));
+  int rc = ep_run(s, kernel, s->ws_hx.as<float>(), s->ws_hw.as<float>(),
+                  out ? s->ws_hout.as<float>() : nullptr, D, steps, tau, stream);
+  if (rc) return rc;
+  if (kernel != EP_KERNEL_SPMV) CU(cudaMemcpyAsync(x, s->ws_hx.p, xb, cudaMemcpyDeviceToHost, st));
+  if (out) CU(cudaMemcpyAsync(out, s->ws_hout.p, xb, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  return EP_OK;
+}
+
+int ep_run_adjoint(ep_schedule* s, const float* x0, const float* w, float* lam, float* grad_w,
+                   int32_t D, int32_t steps, float tau, void* stream) {
+  g_error.clear();
+  if (int rc = check_flux(s, D)) return rc;
+  if (!x0 || !w || !lam || !grad_w) return fail(EP_EINVAL, "null argument");
+  if (steps < 1) return fail(EP_EINVAL, "steps must be >= 1");
+  if (int rc = ensure_device(s)) return rc;
+  cudaStream_t st = as_stream(stream);
+  const ep::HostSchedule& h = s->h;
+  const int32_t R = ep::record_floats(D);
+  const size_t lay = (size_t)h.nd * R;
+  CU(s->ws_hist.ensure(lay * steps * sizeof(float)));
+  CU(s->ws_lam.ensure(lay * sizeof(float)));
+  CU(s->ws_w.ensure((size_t)h.m * sizeof(float)));
+  CU(s->ws_gw.ensure((size_t)h.m * sizeof(float)));
+  if (int rc = ensure_bacc(s, R, st)) return rc;
+  float* hist = s->ws_hist.as<float>();
+  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, D, R, x0, hist, st, s->t()));
+  CU(ep::dev::gather(s->d_perm.as<int32_t>(), h.m, w, s->ws_w.as<float>(), st, s->t()));
+  CU(cudaMemsetAsync(s->ws_gw.p, 0, (size_t)h.m * sizeof(float), st));
+  for (int32_t t = 0; t + 1 < steps; ++t)
+    CU(ep::dev::flux_step(
+        flux_args(s, s->ws_w.as<float>(), hist + lay * t, hist + lay * (t + 1), nullptr, tau), D, st));
+  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, D, R, lam, s->ws_lam.as<float>(), st, s->t()));
+  for (int32_t t = steps - 1; t >= 0; --t)
+    CU(ep::dev::flux_adjoint_step(flux_args(s, s->ws_w.as<float>(), hist + lay * t, nullptr, nullptr, tau),
+                                  D, s->ws_lam.as<float>(), s->ws_gw.as<float>(), st));
+  CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, D, R, s->ws_lam.as<float>(), lam, st, s->t()));
+  CU(ep::dev::scatter_add(s->d_perm.as<int32_t>(), h.m, s->ws_gw.as<float>(), grad_w, st, s->t()));
+  return EP_OK;
+}
+
+int ep_timing(ep_schedule* s, int32_t enable) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (enable == 2) s->timer.clear();
+  s->timer.on = enable != 0;
+  return EP_OK;
+}
+
+int ep_timing_read(ep_schedule* s, int32_t kernel_class, double* total_ms, int64_t* launches) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (kernel_class < 0 || kernel_class >= EP_T_CLASSES) return fail(EP_EINVAL, "bad kernel class");
+  s->timer.collect();
+  if (total_ms) *total_ms = s->timer.total[kernel_class];
+  if (launches) *launches = s->timer.count[kernel_class];
+  return EP_OK;
+}
+
+int ep_set_threads(ep_schedule* s, int32_t threads) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (threads < 32 || threads > 1024 || threads % 32) return fail(EP_EINVAL, "threads = %d", threads);
+  s->tpb = threads;
+  return EP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// kernels.h -- launchers of the device code (internal to libepcache).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace ep {
+namespace dev {
+
+// Optional per-launch timing hook (events recorded on the launch stream).
+struct Timer {
+  virtual void begin(int cls, cudaStream_t st) = 0;
+  virtual void end(int cls, cudaStream_t st) = 0;
+  virtual ~Timer() = default;
+};
+enum { T_EDGE_FWD = 0, T_BND = 1, T_EDGE_ADJ = 2, T_SPMV = 3, T_LAYOUT = 4, T_COST = 5 };
+
+struct FluxArgs {
+  const FluxDesc* desc;
+  int64_t k;
+  const int32_t* flist;
+  const uint32_t* loc;
+  const float* w;      // task weights in schedule order
+  const float* x_in;   // state in schedule layout (R floats per record)
+  float* x_out;        // may equal x_in
+  float* bacc;         // n_bnd * R floats, zero on entry, zero on exit
+  float* out;          // flux in schedule layout or nullptr
+  int64_t n_int, n_bnd;
+  float tau;
+  int32_t max_nv;
+  int tpb;
+  Timer* timer;
+};
+
+struct SpmvArgs {
+  const SpmvDesc* desc;
+  int64_t k;
+  const int32_t* xlist;
+  const int32_t* ylist;
+  const uint32_t* loc;
+  const float* w;
+  const float* x;   // x records
+  float* y;         // y records; [ny_int, ny_int + ny_zero) zeroed first
+  int64_t ny_int, ny_zero;
+  int32_t max_nx, max_ny;
+  int tpb;
+  Timer* timer;
+};
+
+struct CostArgs {
+  const int64_t* block_ptr;
+  int64_t k;
+  const int32_t* eu;  // endpoint ids in schedule order
+  const int32_t* ev;
+  int32_t max_ne;
+  uint8_t* touched;   // nd bytes of workspace
+  int64_t nd;
+  unsigned long long* counters;  // [0] loads, [1] touched
+  Timer* timer;
+};
+
+cudaError_t flux_step(const FluxArgs& a, int D, cudaStream_t st);
+cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st);
+cudaError_t spmv(const SpmvArgs& a, cudaStream_t st);
+cudaError_t layout_in(const int32_t* rec_of, int64_t n, int D, int R, const float* x, float* x_lay,
+                      cudaStream_t st, Timer* t);
+cudaError_t layout_out(const int32_t* rec_of, int64_t n, int D, int R, const float* x_lay, float* x,
+                       cudaStream_t st, Timer* t);
+cudaError_t gather(const int32_t* perm, int64_t m, const float* w, float* w_lay, cudaStream_t st,
+                   Timer* t);
+cudaError_t scatter_add(const int32_t* perm, int64_t m, const float* w_lay, float* w, cudaStream_t st,
+                        Timer* t);
+cudaError_t cost(const CostArgs& a, cudaStream_t st);
+
+}  // namespace dev
+}  // namespace ep

@@ -1,0 +1,266 @@
+// schedule.cpp -- from a task partition to the arrays the kernels use.
+//
+//   reconstruction   tasks grouped by block, ascending id inside a block
+//                    (Definition 4);
+//   vertex lists     distinct data vertices of each block in first-touch
+//                    order (the block's share of the data, Section 4 Fig. 7);
+//   cpack            ids in order of first appearance over blocks (Section
+//                    4.1, after Ding and Kennedy), untouched vertices last;
+//   cost             loads = sum_b |V_b|, vertex cut = loads - touched (Eq. 1);
+//   kernel layout    the cpack order split into vertices one block uses
+//                    (updated in place by that block) and shared vertices
+//                    (accumulated by atomics), plus 16-bit local slots per task.
+#include <algorithm>
+#include <thread>
+
+#include "internal.h"
+
+namespace ep {
+namespace {
+
+// Endpoint pair of task e as data-vertex ids (bipartite: y_i -> n + i).
+inline void task_ends(const HostSchedule& s, int64_t e, int32_t& u, int32_t& v) {
+  const bool bip = (s.flags & 1u) != 0;
+  u = bip ? (int32_t)(s.n + s.src[e]) : s.src[e];
+  v = s.dst[e];
+}
+
+// Per-block first-touch vertex lists, computed block-parallel with one stamp
+// array per worker, then concatenated.
+void vertex_lists(HostSchedule& s, int threads) {
+  const int64_t k = s.k;
+  std::vector<int64_t> count(k, 0);
+  std::vector<std::vector<int32_t>> chunks(threads);
+  std::vector<int64_t> lo(threads + 1);
+  for (int t = 0; t <= threads; ++t) lo[t] = k * t / threads;
+  auto work = [&](int t) {
+    std::vector<int32_t> stamp(s.nd, -1);
+    auto& out = chunks[t];
+    for (int64_t b = lo[t]; b < lo[t + 1]; ++b) {
+      const int64_t before = (int64_t)out.size();
+      for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
+        int32_t u, v;
+        task_ends(s, s.edge_perm[i], u, v);
+        if (stamp[u] != (int32_t)b) {
+          stamp[u] = (int32_t)b;
+          out.push_back(u);
+        }
+        if (stamp[v] != (int32_t)b) {
+          stamp[v] = (int32_t)b;
+          out.push_back(v);
+        }
+      }
+      count[b] = (int64_t)out.size() - before;
+    }
+  };
+  if (threads == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < threads; ++t) pool.emplace_back(work, t);
+    for (auto& th : pool) th.join();
+  }
+  s.vert_ptr.assign(k + 1, 0);
+  for (int64_t b = 0; b < k; ++b) s.vert_ptr[b + 1] = s.vert_ptr[b] + count[b];
+  s.vert_list.clear();
+  s.vert_list.reserve(s.vert_ptr[k]);
+  for (auto& c : chunks) s.vert_list.insert(s.vert_list.end(), c.begin(), c.end());
+  s.loads = s.vert_ptr[k];
+}
+
+void cpack(HostSchedule& s) {
+  s.relabel.assign(s.nd, -1);
+  int32_t next = 0;
+  for (int32_t v : s.vert_list)
+    if (s.relabel[v] < 0) s.relabel[v] = next++;
+  s.touched = next;
+  for (int64_t v = 0; v < s.nd; ++v)
+    if (s.relabel[v] < 0) s.relabel[v] = next++;
+}
+
+// Number of blocks using each vertex (p_v) and the first such block.
+void usage(const HostSchedule& s, std::vector<int32_t>& p, std::vector<int32_t>& owner) {
+  p.assign(s.nd, 0);
+  owner.assign(s.nd, -1);
+  for (int64_t b = 0; b < s.k; ++b)
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      if (p[v]++ == 0) owner[v] = (int32_t)b;
+    }
+}
+
+std::string flux_layout(HostSchedule& s) {
+  std::vector<int32_t> p, owner;
+  usage(s, p, owner);
+  s.rec_of.assign(s.nd, -1);
+  s.fdesc.assign(s.k, FluxDesc{});
+  int32_t next = 0;
+  for (int64_t b = 0; b < s.k; ++b) {
+    s.fdesc[b].int_lo = next;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      if (owner[v] == b && p[v] == 1) s.rec_of[v] = next++;
+    }
+    s.fdesc[b].n_int = next - s.fdesc[b].int_lo;
+  }
+  s.n_int = next;
+  for (int64_t b = 0; b < s.k; ++b) {
+    s.fdesc[b].bnd_lo = next;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      if (owner[v] == b && p[v] > 1) s.rec_of[v] = next++;
+    }
+    s.fdesc[b].n_ob = next - s.fdesc[b].bnd_lo;
+  }
+  s.n_bnd = next - s.n_int;
+  for (int64_t v = 0; v < s.nd; ++v)
+    if (s.rec_of[v] < 0) s.rec_of[v] = next++;
+  // foreign lists, local slots and packed task slots
+  s.flist.clear();
+  s.loc.assign(s.m, 0);
+  s.max_nv = 0;
+  std::vector<int32_t> slot(s.nd, -1);
+  for (int64_t b = 0; b < s.k; ++b) {
+    FluxDesc& d = s.fdesc[b];
+    d.e0 = (int32_t)s.block_ptr[b];
+    d.ne = (int32_t)(s.block_ptr[b + 1] - s.block_ptr[b]);
+    d.f0 = (int32_t)s.flist.size();
+    const int32_t own = d.n_int + d.n_ob;
+    int32_t nf = 0;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      const int32_t r = s.rec_of[v];
+      if (owner[v] == b)
+        slot[v] = r < s.n_int ? r - d.int_lo : d.n_int + (r - d.bnd_lo);
+      else {
+        slot[v] = own + nf++;
+        s.flist.push_back(r);
+      }
+    }
+    d.nf = nf;
+    const int32_t nv = own + nf;
+    if (nv > 65535) return "block touches more than 65535 vertices";
+    s.max_nv = std::max(s.max_nv, nv);
+    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
+      int32_t u, v;
+      task_ends(s, s.edge_perm[i], u, v);
+      s.loc[i] = (uint32_t)slot[u] | ((uint32_t)slot[v] << 16);
+    }
+  }
+  return "";
+}
+
+std::string spmv_layout(HostSchedule& s) {
+  std::vector<int32_t> p, owner;
+  usage(s, p, owner);
+  const int32_t n = (int32_t)s.n;
+  s.xrec_of.assign(n, -1);
+  s.yrec_of.assign(n, -1);
+  s.sdesc.assign(s.k, SpmvDesc{});
+  // x records: cpack order restricted to columns
+  int32_t nx = 0;
+  for (int64_t b = 0; b < s.k; ++b) {
+    SpmvDesc& d = s.sdesc[b];
+    d.x_lo = nx;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      if (v < n && owner[v] == b) s.xrec_of[v] = nx++;
+    }
+    d.n_xo = nx - d.x_lo;
+  }
+  for (int32_t j = 0; j < n; ++j)
+    if (s.xrec_of[j] < 0) s.xrec_of[j] = nx++;
+  // y records: single-block rows first, then shared rows
+  int32_t ny = 0;
+  for (int64_t b = 0; b < s.k; ++b) {
+    SpmvDesc& d = s.sdesc[b];
+    d.yi_lo = ny;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      if (v >= n && owner[v] == b && p[v] == 1) s.yrec_of[v - n] = ny++;
+    }
+    d.n_yi = ny - d.yi_lo;
+  }
+  s.ny_int = ny;
+  for (int64_t b = 0; b < s.k; ++b) {
+    SpmvDesc& d = s.sdesc[b];
+    d.yb_lo = ny;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      if (v >= n && owner[v] == b && p[v] > 1) s.yrec_of[v - n] = ny++;
+    }
+    d.n_yob = ny - d.yb_lo;
+  }
+  s.ny_bnd = ny - s.ny_int;
+  for (int32_t i = 0; i < n; ++i)
+    if (s.yrec_of[i] < 0) s.yrec_of[i] = ny++;
+  s.xlist.clear();
+  s.ylist.clear();
+  s.loc.assign(s.m, 0);
+  s.max_nx = s.max_ny = 0;
+  std::vector<int32_t> slot(s.nd, -1);
+  for (int64_t b = 0; b < s.k; ++b) {
+    SpmvDesc& d = s.sdesc[b];
+    d.e0 = (int32_t)s.block_ptr[b];
+    d.ne = (int32_t)(s.block_ptr[b + 1] - s.block_ptr[b]);
+    d.fx0 = (int32_t)s.xlist.size();
+    d.fy0 = (int32_t)s.ylist.size();
+    int32_t nxf = 0, nyf = 0;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      if (v < n) {
+        if (owner[v] == b)
+          slot[v] = s.xrec_of[v] - d.x_lo;
+        else {
+          slot[v] = d.n_xo + nxf++;
+          s.xlist.push_back(s.xrec_of[v]);
+        }
+      } else {
+        const int32_t r = s.yrec_of[v - n];
+        if (owner[v] == b)
+          slot[v] = r < s.ny_int ? r - d.yi_lo : d.n_yi + (r - d.yb_lo);
+        else {
+          slot[v] = d.n_yi + d.n_yob + nyf++;
+          s.ylist.push_back(r);
+        }
+      }
+    }
+    d.n_xf = nxf;
+    d.n_yf = nyf;
+    const int32_t nxs = d.n_xo + nxf, nys = d.n_yi + d.n_yob + nyf;
+    if (nxs > 65535 || nys > 65535) return "block touches more than 65535 vertices";
+    s.max_nx = std::max(s.max_nx, nxs);
+    s.max_ny = std::max(s.max_ny, nys);
+    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
+      int32_t u, v;
+      task_ends(s, s.edge_perm[i], u, v);
+      s.loc[i] = (uint32_t)slot[u] | ((uint32_t)slot[v] << 16);  // (y slot, x slot)
+    }
+  }
+  return "";
+}
+
+}  // namespace
+
+std::string build_schedule(HostSchedule& s, int threads) {
+  if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+  threads = (int)std::max<int64_t>(1, std::min<int64_t>(threads, s.k));
+  // reconstruction (Definition 4): counting sort by block keeps ascending ids
+  s.block_ptr.assign(s.k + 1, 0);
+  for (int64_t e = 0; e < s.m; ++e) ++s.block_ptr[s.part[e] + 1];
+  s.max_ne = 0;
+  for (int64_t b = 0; b < s.k; ++b) {
+    s.max_ne = std::max<int32_t>(s.max_ne, (int32_t)s.block_ptr[b + 1]);
+    s.block_ptr[b + 1] += s.block_ptr[b];
+  }
+  s.edge_perm.assign(s.m, 0);
+  {
+    std::vector<int64_t> cur(s.block_ptr.begin(), s.block_ptr.end() - 1);
+    for (int64_t e = 0; e < s.m; ++e) s.edge_perm[cur[s.part[e]]++] = (int32_t)e;
+  }
+  vertex_lists(s, threads);
+  cpack(s);
+  return (s.flags & 1u) ? spmv_layout(s) : flux_layout(s);
+}
+
+}  // namespace ep

@@ -1,0 +1,228 @@
+"""CUDA path vs the CPU oracle, through the C ABI (GPU only).
+
+Integers (schedule, vertex lists, relabel, cost) must be bit-exact; FP32
+states and gradients must be within 1e-5 relative L2 of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU machines, skipped there
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1605_02043_gb300 as E  # noqa: E402
+
+RTOL = 1e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+@pytest.fixture(scope="module")
+def small_mesh():
+    src, dst = W.knn_mesh(4096, 4, 0)
+    return src, dst, 4096
+
+
+def check_schedule_matches_oracle(S, ref):
+    a = S.arrays()
+    for key in ("block_ptr", "edge_perm", "vert_ptr", "vert_list", "relabel"):
+        assert np.array_equal(a[key], ref[key]), key
+    assert (a["loads"], a["cut"]) == (ref["loads"], ref["cut"])
+    assert S.cost() == (ref["loads"], ref["cut"])  # GPU sort/unique count
+
+
+@pytest.mark.parametrize("C", [256, 64, 1000])
+@pytest.mark.parametrize("default_order", [False, True])
+def test_flux_one_step_small_mesh(small_mesh, C, default_order):
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, C, default_order=default_order)
+    check_schedule_matches_oracle(S, O.ep_schedule(src, dst, n, C, default_order=default_order))
+    x0 = W.flux_state(n, 5, 0)
+    w = W.flux_weights(src.size, 0)
+    x = cuda(x0)
+    out = torch.zeros_like(x)
+    S.run(x, cuda(w), out, steps=1, tau=1e-3)
+    x1, f0 = O.flux_steps(src, dst, x0, w, 1, 1e-3)
+    assert rel_l2(out.cpu().numpy(), f0) <= RTOL
+    assert rel_l2(x.cpu().numpy(), x1) <= RTOL
+    # the increment itself, not only the state, must match
+    assert rel_l2(x.cpu().numpy() - x0, x1 - x0) <= 1e-4
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 6, 8])
+def test_flux_state_widths(small_mesh, D):
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 256)
+    x0 = W.flux_state(n, D, 3)
+    w = W.flux_weights(src.size, 3)
+    x = cuda(x0)
+    out = torch.zeros_like(x)
+    S.run(x, cuda(w), out, steps=3, tau=1e-2)
+    xT, fT = O.flux_steps(src, dst, x0, w, 3, 1e-2)
+    assert rel_l2(out.cpu().numpy(), fT) <= RTOL
+    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
+
+
+def test_flux_tau_zero_is_pure_flux(small_mesh):
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 128)
+    x0 = W.flux_state(n, 5, 1)
+    w = W.flux_weights(src.size, 1)
+    x = cuda(x0)
+    out = torch.zeros_like(x)
+    S.run(x, cuda(w), out, steps=2, tau=0.0)
+    assert torch.equal(x.cpu(), torch.from_numpy(x0))
+    assert rel_l2(out.cpu().numpy(), O.flux(src, dst, x0, w)) <= RTOL
+
+
+def test_flux_edge_cases():
+    # self loops, repeated pairs, isolated vertices, C = 1 and a single block
+    rng = np.random.default_rng(4)
+    n = 300
+    src = rng.integers(0, 200, 777).astype(np.int32)
+    dst = rng.integers(0, 200, 777).astype(np.int32)
+    src[:20] = dst[:20]  # self loops
+    src[20:40], dst[20:40] = src[40:60], dst[40:60]  # repeated pairs
+    x0 = W.flux_state(n, 5, 2)
+    w = W.flux_weights(src.size, 2)
+    x1, f0 = O.flux_steps(src, dst, x0, w, 2, 1e-2)
+    for C in (1, 7, 100, 777, 5000):
+        S = E.Schedule.partition(src, dst, n, C)
+        check_schedule_matches_oracle(S, O.ep_schedule(src, dst, n, C))
+        x = cuda(x0)
+        out = torch.zeros_like(x)
+        S.run(x, cuda(w), out, steps=2, tau=1e-2)
+        assert rel_l2(out.cpu().numpy(), f0) <= RTOL, C
+        assert rel_l2(x.cpu().numpy(), x1) <= RTOL, C
+        assert np.array_equal(x.cpu().numpy()[:, 200:], x0[:, 200:])  # untouched
+
+
+def test_layout_round_trip(small_mesh):
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 256)
+    for D in (1, 3, 5, 8):
+        x = cuda(W.flux_state(n, D, 5))
+        lay = torch.full((S.layout_floats(D),), 7.0, device="cuda")
+        S.layout_in(x, lay)
+        back = torch.zeros_like(x)
+        S.layout_out(lay, back)
+        assert torch.equal(back, x)
+        R = E.record_floats(D)
+        if R > D:
+            assert torch.all(lay.view(-1, R)[:, D:] == 0)
+
+
+def test_step_api_matches_run(small_mesh):
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 256)
+    x0 = W.flux_state(n, 5, 6)
+    w = W.flux_weights(src.size, 6)
+    xl = torch.zeros(S.layout_floats(5), device="cuda")
+    wl = torch.zeros(S.m, device="cuda")
+    ol = torch.zeros_like(xl)
+    S.layout_in(cuda(x0), xl)
+    S.weights_in(cuda(w), wl)
+    x2 = torch.empty_like(xl)
+    S.step(5, xl, x2, wl, ol, tau=1e-3)  # out of place
+    S.step(5, x2, x2, wl, ol, tau=1e-3)  # in place
+    x = torch.zeros(5, n, device="cuda")
+    S.layout_out(x2, x)
+    out = torch.zeros_like(x)
+    S.layout_out(ol, out)
+    xT, fT = O.flux_steps(src, dst, x0, w, 2, 1e-3)
+    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
+    assert rel_l2(out.cpu().numpy(), fT) <= RTOL
+
+
+@pytest.mark.parametrize("C,default_order", [(512, False), (512, True), (64, False)])
+def test_spmv_rmat(C, default_order):
+    scale = 12
+    n = 1 << scale
+    r, c = W.rmat(scale=scale, m_draws=1 << 16, seed=1)
+    x0, w = W.spmv_inputs(n, r.size, 0)
+    S = E.Schedule.partition(r, c, n, C, bipartite=True, default_order=default_order)
+    check_schedule_matches_oracle(S, O.ep_schedule(r, c, n, C, bipartite=True,
+                                                   default_order=default_order))
+    y = torch.full((n,), 3.0, device="cuda")
+    S.run(cuda(x0), cuda(w), y, kernel=E.SPMV)
+    ref = O.spmv(r, c, x0, w, n)
+    assert rel_l2(y.cpu().numpy(), ref) <= RTOL
+    # rows without tasks are zero
+    empty = np.setdiff1d(np.arange(n), r)
+    assert torch.all(y[torch.from_numpy(empty).cuda()] == 0)
+
+
+def test_adjoint_matches_oracle(small_mesh):
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 256)
+    x0 = W.flux_state(n, 5, 0)
+    w = W.flux_weights(src.size, 0)
+    g = W.loss_weights(n, 5, 1)
+    T, tau = 10, 1e-3
+    dx_ref, dw_ref = O.flux_adjoint(src, dst, x0, w, T, tau, g)
+    lam = cuda(g)
+    gw = torch.zeros(src.size, device="cuda")
+    S.run_adjoint(cuda(x0), cuda(w), lam, gw, steps=T, tau=tau)
+    assert rel_l2(lam.cpu().numpy(), dx_ref) <= RTOL
+    assert rel_l2(gw.cpu().numpy(), dw_ref) <= RTOL
+    # the part of dL/dx0 that the flux adds on top of g
+    assert rel_l2(lam.cpu().numpy() - g, dx_ref - g) <= 1e-4
+
+
+def test_run_host_matches_device(small_mesh):
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 256)
+    x0 = W.flux_state(n, 5, 7)
+    w = W.flux_weights(src.size, 7)
+    xh = torch.from_numpy(x0.copy()).pin_memory()
+    wh = torch.from_numpy(w.copy()).pin_memory()
+    oh = torch.zeros_like(xh).pin_memory()
+    S.run_host(xh, wh, oh, steps=4, tau=1e-3, D=5)
+    xT, fT = O.flux_steps(src, dst, x0, w, 4, 1e-3)
+    assert rel_l2(xh.numpy(), xT) <= RTOL
+    assert rel_l2(oh.numpy(), fT) <= RTOL
+
+
+def test_batch_schedule(small_mesh):
+    meshes = [W.knn_mesh(nn, 4, 50 + i) for i, nn in enumerate((700, 1500, 2300))]
+    parts = [E.Schedule.partition(s, d, nn, C) for (s, d), nn, C in
+             zip(meshes, (700, 1500, 2300), (64, 128, 256))]
+    B = E.Schedule.batch(parts)
+    offs = np.cumsum([0, 700, 1500])
+    src = np.concatenate([s + o for (s, _), o in zip(meshes, offs)]).astype(np.int32)
+    dst = np.concatenate([d + o for (_, d), o in zip(meshes, offs)]).astype(np.int32)
+    n = 4500
+    assert B.k == sum(p.k for p in parts)
+    assert B.cost()[0] == sum(p.cost()[0] for p in parts)
+    x0 = W.flux_state(n, 5, 8)
+    w = W.flux_weights(src.size, 8)
+    x = cuda(x0)
+    B.run(x, cuda(w), None, steps=3, tau=1e-3)
+    xT, _ = O.flux_steps(src, dst, x0, w, 3, 1e-3)
+    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
+
+
+def test_errors_are_reported(small_mesh):
+    src, dst, n = small_mesh
+    with pytest.raises(E.EpError):
+        E.Schedule.partition(src, dst, n, 0)
+    S = E.Schedule.partition(src, dst, n, 256)
+    x = torch.zeros(9, n, device="cuda")
+    with pytest.raises(E.EpError):
+        S.run(x, torch.zeros(S.m, device="cuda"), None)  # D = 9 > EP_MAX_D
+    with pytest.raises(E.EpError):
+        S.run(torch.zeros(n, device="cuda"), torch.zeros(S.m, device="cuda"),
+              torch.zeros(n, device="cuda"), kernel=E.SPMV)  # not bipartite
