@@ -5,8 +5,9 @@ Workload: the 1M-node mesh (1,048,576 points uniform in the unit cube, seed
 0, symmetrised k=4 nearest-neighbour graph, ~2.57M tasks in shuffled order),
 state x: 5 x fp32 N(0,1), weights w ~ U(0.5, 1.5), explicit steps
 x <- x + 1e-3 * flux(x).  One bench step is one explicit step (edge kernel
-plus shared-vertex update) on the whole mesh, with L2 flushed (a write of
-twice the L2 size) before every timed step and outside its events.
+plus shared-vertex update) on the whole mesh, with L2 flushed (a write and
+then a read of scratch buffers twice the L2 size) before every timed step and
+outside its events.
 
 Reported (one JSON line on rank 0):
   value        forward edge updates/s, partitioned schedule (C = --C)
@@ -49,10 +50,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--C", type=int, default=256)
-    ap.add_argument("--threads", type=int, default=256)
+    ap.add_argument("--threads", type=int, default=128, help="consumer threads per CUDA block")
+    ap.add_argument("--stages", type=int, default=2, help="0: one CUDA block per schedule block")
     ap.add_argument("--n", type=int, default=1 << 20, help="mesh points (default: the 1M-node mesh)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--sweep", action="store_true", help="also time C in {256, 512, 1024}")
+    ap.add_argument("--only", default="", choices=["", "fwd"],
+                    help="fwd: time only the forward loops (for profiler runs)")
     return ap.parse_args()
 
 
@@ -115,16 +119,28 @@ class Clocks:
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
                 "samples": len(rows), "reasons": reasons}
 
 
-def l2_flusher(torch):
-    l2 = torch.cuda.get_device_properties(0).L2_cache_size
-    buf = torch.empty(max(2 * l2, 64 << 20) // 4, dtype=torch.float32, device="cuda")
-    return buf, 2 * l2
+class L2Flush:
+    """Write a buffer twice the L2 size, then read a second one of that size.
+
+    The write evicts everything the previous step left in L2; the read then
+    evicts the write's own dirty lines, so the next timed step starts from a
+    cold, clean L2 and does not pay for the flush's write-backs."""
+
+    def __init__(self, torch):
+        l2 = torch.cuda.get_device_properties(0).L2_cache_size
+        self.bytes = max(2 * l2, 64 << 20)
+        self.a = torch.empty(self.bytes // 4, dtype=torch.float32, device="cuda")
+        self.b = torch.zeros(self.bytes // 4, dtype=torch.float32, device="cuda")
+
+    def __call__(self):
+        self.a.zero_()
+        self.b.sum()
 
 
 def timed_loop(torch, body, steps, warmup, flush):
@@ -135,7 +151,7 @@ def timed_loop(torch, body, steps, warmup, flush):
     torch.cuda.synchronize()
     barrier(torch)
     for a, b in ev:
-        flush.zero_()
+        flush()
         a.record()
         body()
         b.record()
@@ -170,7 +186,7 @@ def bench_fwd(torch, E, S, x0, w, steps, warmup, flush):
     x = torch.from_numpy(x0).cuda()
     wt = torch.from_numpy(w).cuda()
     xl = torch.empty(S.layout_floats(D), device="cuda")
-    wl = torch.empty(S.m, device="cuda")
+    wl = torch.empty(S.weights_floats(), device="cuda")
     S.layout_in(x, xl)
     S.weights_in(wt, wl)
     for _ in range(warmup):
@@ -285,15 +301,26 @@ def main():
     Sd = E.Schedule.partition(src, dst, n, args.C, default_order=True)
     for s in (S, Sd):
         s.set_threads(args.threads)
+        s.set_pipeline(args.stages)
     loads, cut = S.cost()
     loads_d, cut_d = Sd.cost()
     assert (loads, cut) == S.cost_host() and (loads_d, cut_d) == Sd.cost_host()
-    flush, flush_bytes = l2_flusher(torch)
+    flush = L2Flush(torch)
+    flush_bytes = flush.bytes
 
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     fwd = bench_fwd(torch, E, S, x0, w, args.steps, args.warmup, flush)
     fwd_d = bench_fwd(torch, E, Sd, x0, w, args.steps, args.warmup, flush)
+    if args.only == "fwd":
+        clocks.stop()
+        if rank == 0:
+            print(json.dumps({"only": "fwd", "n": n, "m": m, "C": args.C, "threads": args.threads,
+                              "partitioned_edge_ms": fwd["edge_ms"], "default_edge_ms": fwd_d["edge_ms"],
+                              "partitioned_step_ms": statistics.mean(fwd["ms"]),
+                              "default_step_ms": statistics.mean(fwd_d["ms"]),
+                              "loads": loads, "loads_default": loads_d}))
+        return
     iters = max(3, args.steps // 20)
     fb = bench_fwd_bwd(torch, S, x0, w, iters, 3, flush)
     fb_d = bench_fwd_bwd(torch, Sd, x0, w, iters, 3, flush)
@@ -304,6 +331,7 @@ def main():
         for C in (256, 512, 1024):
             Sc = E.Schedule.partition(src, dst, n, C)
             Sc.set_threads(args.threads)
+            Sc.set_pipeline(args.stages)
             r = bench_fwd(torch, E, Sc, x0, w, max(10, args.steps // 4), args.warmup, flush)
             sweep[str(C)] = dict(edge_updates_per_s=m * len(r["ms"]) / (1e-3 * sum(r["ms"])),
                                  loads=Sc.cost_host()[0])
@@ -343,13 +371,15 @@ def main():
         "config": {
             "workload": f"kNN mesh n={n} k=4 (m={m}), D=5, one explicit flux step per bench step",
             "schedule": "edge partition (clone-and-connect + recursive bisection)",
-            "C": args.C, "threads_per_block": args.threads, "tau": TAU,
-            "l2": f"flushed before every timed step ({flush_bytes >> 20} MiB write, outside the events)",
+            "C": args.C, "consumer_threads": args.threads, "pipeline_stages": args.stages, "tau": TAU,
+            "l2": f"flushed before every timed step ({flush_bytes >> 20} MiB write then "
+                  f"{flush_bytes >> 20} MiB read of scratch buffers, outside the events)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "flux_fwd_kernel<5,8>", "algorithmic_bytes_per_launch": alg,
+                     "kernel": "flux_fwd_tma_kernel<5>" if args.stages else "flux_fwd_kernel<5>",
+                     "algorithmic_bytes_per_launch": alg,
                      "launch_ms": fwd["edge_ms"], "peak_kind": f"{peak_kind} HBM copy"},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -39,7 +39,7 @@ extern "C" {
 #define EP_EINVAL (-1)   /* bad argument (sizes, ids out of range, flags) */
 #define EP_ENOMEM (-2)   /* host or device allocation failed */
 #define EP_ECUDA (-3)    /* a CUDA runtime call failed (message has details) */
-#define EP_ETIMEOUT (-4) /* an optimisation thread missed its deadline */
+#define EP_ETIMEOUT (-4) /* a bounded wait expired (device kernel or host thread) */
 #define EP_ENODEV (-5)   /* no CUDA device */
 
 /* ep_partition flags */
@@ -146,22 +146,28 @@ int ep_run_adjoint(ep_schedule *s, const float *x0, const float *w, float *lam, 
                    int32_t D, int32_t steps, float tau, void *stream);
 
 /* ----------------------------------------------------- schedule layout API
- * The kernels work on the schedule's own layout (the paper's opt_arrayA):
- * every touched vertex is a record of R = ep_record_floats(D) floats
- * (R = 1, 2, 4 or 8 >= D, padding lanes zero), ordered by cpack with the
- * vertices used by one block only placed first.  Tasks are in edge_perm order.
- * Keeping state in this layout across calls avoids the permutations.
+ * The kernels work on the schedule's own layout (the paper's opt_arrayA,
+ * Section 4.1): records in cpack order with the vertices used by one block
+ * only placed first, and the D components of every record split into planes
+ * of width 4, 2 and 1 (D = 4a + 2b + c): plane k is a contiguous array of
+ * n_rec records of its width, so a buffer is n_rec * D floats, unpadded.
+ * Task weights use ep_weights_floats(s) floats (edge_perm order, padded per
+ * block).  Keeping state in this layout across calls avoids the permutations.
  */
 int32_t ep_record_floats(int32_t D);
-/* Floats needed for one state buffer in schedule layout (n_records * R). */
+/* Floats needed for one state buffer in schedule layout (n_records * D). */
 int64_t ep_layout_floats(const ep_schedule *s, int32_t D);
-/* x_lay <- x (caller layout float[D][n]); padding lanes zeroed. */
+/* x_lay <- x (caller layout float[D][n]). */
 int ep_layout_in(ep_schedule *s, int32_t D, const float *x, float *x_lay, void *stream);
 /* x <- x_lay (caller layout float[D][n]). */
 int ep_layout_out(ep_schedule *s, int32_t D, const float *x_lay, float *x, void *stream);
-/* w_lay[i] <- w[edge_perm[i]]. */
+/* Floats of a task-weight buffer in schedule layout: tasks in edge_perm order,
+ * each block's run starting on a 16-byte boundary (flux schedules; zero-filled
+ * padding between runs), or exactly m for SpMV schedules. */
+int64_t ep_weights_floats(const ep_schedule *s);
+/* w_lay <- w permuted into schedule layout (padding slots get 0). */
 int ep_weights_in(ep_schedule *s, const float *w, float *w_lay, void *stream);
-/* w[edge_perm[i]] += w_lay[i]. */
+/* w[task] += w_lay[slot of task] for every task (padding slots ignored). */
 int ep_weights_out_add(ep_schedule *s, const float *w_lay, float *w, void *stream);
 
 /*
@@ -211,6 +217,26 @@ int ep_timing_read(ep_schedule *s, int32_t kernel_class, double *total_ms, int64
 /* Threads per CUDA block of the edge kernels (32..1024, multiple of 32;
  * default 256).  Does not change results beyond FP32 rounding order. */
 int ep_set_threads(ep_schedule *s, int32_t threads);
+
+/*
+ * Edge-kernel organisation for flux steps.  stages = 0: one CUDA block per
+ * schedule block (stage, compute, write back).  stages = 2..4 (default 2):
+ * persistent CUDA blocks; a producer warp fills a ring of that many
+ * shared-memory stages with 1-D TMA bulk copies of each schedule block's
+ * contiguous pieces and pulls the block `ahead` positions later (0..64,
+ * default 4) into L2; consumer warps (ep_set_threads) gather foreign records
+ * with cp.async and compute one stage while the next ones load.  Results
+ * agree up to FP32 rounding order.
+ */
+int ep_set_pipeline(ep_schedule *s, int32_t stages, int32_t ahead);
+
+/*
+ * Reads and clears the error word of the pipelined kernels (synchronises
+ * `stream`): every wait inside them is bounded, and an expired wait sets a
+ * bit here instead of hanging (bit 0: waiting for data, bit 1: waiting for a
+ * free stage).  *code = 0 and EP_OK when clean, else EP_ETIMEOUT.
+ */
+int ep_check_errors(ep_schedule *s, int32_t *code, void *stream);
 
 void ep_schedule_free(ep_schedule *s);
 

@@ -179,6 +179,17 @@ class Schedule:
     def set_threads(self, threads: int):
         check(lib().ep_set_threads(self._h, threads))
 
+    def set_pipeline(self, stages: int, ahead: int = 4):
+        """0: one CUDA block per schedule block; 2..4: persistent pipelined kernel
+        with `ahead` schedule blocks of L2 prefetch."""
+        check(lib().ep_set_pipeline(self._h, stages, ahead))
+
+    def check_errors(self, stream=None) -> int:
+        """Error word of the pipelined kernels (raises EpError when non-zero)."""
+        code = ctypes.c_int32()
+        check(lib().ep_check_errors(self._h, ctypes.byref(code), _stream(stream)))
+        return code.value
+
     def timing(self, enable: int = 2):
         """Start (2 = clear and start), keep (1) or stop (0) per-kernel timing."""
         check(lib().ep_timing(self._h, enable))
@@ -192,6 +203,10 @@ class Schedule:
     # ------------------------------------------------------ schedule layout
     def layout_floats(self, D: int) -> int:
         return int(lib().ep_layout_floats(self._h, D))
+
+    def weights_floats(self) -> int:
+        """Length of a task-weight buffer in schedule layout."""
+        return int(lib().ep_weights_floats(self._h))
 
     def layout_in(self, x, x_lay, stream=None):
         check(lib().ep_layout_in(self._h, int(x.shape[0]), _vp(x), _vp(x_lay), _stream(stream)))

@@ -30,6 +30,7 @@ SIGNATURES = {
     "ep_run_adjoint": (ctypes.c_int, [P, P, P, P, P, I32, I32, F32, P]),
     "ep_record_floats": (I32, [I32]),
     "ep_layout_floats": (I64, [P, I32]),
+    "ep_weights_floats": (I64, [P]),
     "ep_layout_in": (ctypes.c_int, [P, I32, P, P, P]),
     "ep_layout_out": (ctypes.c_int, [P, I32, P, P, P]),
     "ep_weights_in": (ctypes.c_int, [P, P, P, P]),
@@ -40,6 +41,8 @@ SIGNATURES = {
     "ep_timing": (ctypes.c_int, [P, I32]),
     "ep_timing_read": (ctypes.c_int, [P, I32, P, P]),
     "ep_set_threads": (ctypes.c_int, [P, I32]),
+    "ep_set_pipeline": (ctypes.c_int, [P, I32, I32]),
+    "ep_check_errors": (ctypes.c_int, [P, P, P]),
     "ep_schedule_free": (None, [P]),
 }
 

@@ -21,7 +21,7 @@ class FluxSteps(torch.autograd.Function):
         x0 = x0.contiguous()
         w = w.contiguous()
         xl = torch.empty(sched.layout_floats(D), device=x0.device, dtype=torch.float32)
-        wl = torch.empty(sched.m, device=x0.device, dtype=torch.float32)
+        wl = torch.empty(sched.weights_floats(), device=x0.device, dtype=torch.float32)
         sched.layout_in(x0, xl)
         sched.weights_in(w, wl)
         ckpts = []

@@ -9,7 +9,7 @@
 #include <string>
 #include <thread>
 
-#include "../../include/epcache.h"
+#include "epcache.h"
 #include "internal.h"
 #include "kernels.h"
 
@@ -132,12 +132,17 @@ struct ep_schedule {
   int tpb = 256;
   bool bacc_dirty = true;
   // device copy of the schedule
-  DBuf d_desc, d_flist, d_ylist, d_loc, d_perm, d_rec, d_xrec, d_yrec, d_bptr, d_eu, d_ev;
+  DBuf d_desc, d_flist, d_ylist, d_loc, d_inc, d_ptr, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
+      d_ev;
   // workspace
   DBuf ws_x, ws_out, ws_w, ws_bacc, ws_lam, ws_gw, ws_hist, ws_flags, ws_cnt;
   DBuf ws_hx, ws_hw, ws_hout;
   EventTimer timer;
   ep::dev::Timer* t() { return timer.on ? &timer : nullptr; }
+  int stages = 2;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
+  int ahead = 4;   // L2 prefetch distance of the pipelined kernels, in schedule blocks per CUDA block
+  DBuf ws_ctl;     // [0] block counter, [1] error word
+  int sm_count = 0;
 };
 
 namespace {
@@ -178,8 +183,8 @@ int ensure_device(ep_schedule* s) {
   CU(upload(s->d_ev, ev));
   CU(upload(s->d_bptr, h.block_ptr));
   CU(upload(s->d_perm, h.edge_perm));
-  CU(upload(s->d_loc, h.loc));
   if (bipartite(s)) {
+    CU(upload(s->d_loc, h.loc));
     CU(upload(s->d_desc, h.sdesc));
     CU(upload(s->d_flist, h.xlist));
     CU(upload(s->d_ylist, h.ylist));
@@ -188,6 +193,9 @@ int ensure_device(ep_schedule* s) {
   } else {
     CU(upload(s->d_desc, h.fdesc));
     CU(upload(s->d_flist, h.flist));
+    CU(upload(s->d_inc, h.inc));
+    CU(upload(s->d_ptr, h.ptr));
+    CU(upload(s->d_wmap, h.wmap));
     CU(upload(s->d_rec, h.rec_of));
   }
   s->device = dev;
@@ -196,25 +204,79 @@ int ensure_device(ep_schedule* s) {
 
 cudaStream_t as_stream(void* p) { return static_cast<cudaStream_t>(p); }
 
+// weight layout: flux schedules use the padded per-block layout (wmap),
+// SpMV schedules the plain schedule order (edge_perm)
+const int32_t* wmap_of(ep_schedule* s) {
+  return bipartite(s) ? s->d_perm.as<int32_t>() : s->d_wmap.as<int32_t>();
+}
+int64_t wlen_of(const ep_schedule* s) { return bipartite(s) ? s->h.m : s->h.w_pad; }
+
 ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, float* x_out,
                             float* out, float tau) {
   ep::dev::FluxArgs a;
   a.desc = s->d_desc.as<ep::FluxDesc>();
   a.k = s->h.k;
   a.flist = s->d_flist.as<int32_t>();
-  a.loc = s->d_loc.as<uint32_t>();
+  a.inc = s->d_inc.as<uint32_t>();
+  a.ptr = s->d_ptr.as<uint16_t>();
   a.w = w;
   a.x_in = x_in;
   a.x_out = x_out;
   a.bacc = s->ws_bacc.as<float>();
   a.out = out;
+  a.n_rec = s->h.n_rec;
   a.n_int = s->h.n_int;
   a.n_bnd = s->h.n_bnd;
   a.tau = tau;
-  a.max_nv = s->h.max_nv;
+  a.max_np = s->h.max_nv;
+  a.max_ne = s->h.max_ne;
+  a.max_nent = s->h.max_nent;
   a.tpb = s->tpb;
   a.timer = s->t();
   return a;
+}
+
+// Stage layout and grid of the pipelined kernels for state width D.
+int tma_plan(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
+  const ep::HostSchedule& h = s->h;
+  auto up = [](int64_t x, int64_t m) { return (x + m - 1) / m * m; };
+  ep::dev::TmaLayout& L = P.L;
+  L.npos = (int)up(h.max_nv, 4);
+  const int64_t xb = (int64_t)D * L.npos * 4;
+  L.off_lam = (int)xb;
+  L.off_w = (int)(L.off_lam + (adjoint ? xb : 0));
+  L.off_ent = (int)(L.off_w + up(h.max_ne, 4) * 4);
+  L.off_ptr = (int)(L.off_ent + up(h.max_nent, 4) * 4);
+  L.off_flist = (int)(L.off_ptr + up(h.max_nv + 1, 8) * 2);
+  L.off_desc = (int)(L.off_flist + up(h.max_nf, 4) * 4);
+  L.stage_bytes = (int)up(L.off_desc + (int64_t)sizeof(ep::FluxDesc) + 16, 128);
+  if (!s->sm_count) {
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  }
+  int optin = 0, dev = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  L.stages = std::min(s->stages, ep::dev::kMaxStages);
+  L.ahead = s->ahead;
+  while (L.stages > 1 && (int64_t)L.stages * L.stage_bytes > optin) --L.stages;
+  if ((int64_t)L.stages * L.stage_bytes > optin)
+    return fail(EP_EINVAL, "a schedule block needs %d bytes of shared memory (limit %d)", L.stage_bytes, optin);
+  P.smem = (size_t)L.stages * L.stage_bytes;
+  P.threads = 32 * (L.ahead > 0 ? 2 : 1) + s->tpb;  // producer (+ prefetch) warp, consumer warps
+  const void* kern = ep::dev::flux_tma_kernel_ptr(D, adjoint);
+  CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+  int per_sm = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P.threads, P.smem));
+  if (per_sm < 1) return fail(EP_EINVAL, "pipelined kernel does not fit on an SM");
+  P.grid = (int)std::min<int64_t>(h.k, (int64_t)per_sm * s->sm_count);
+  if (!s->ws_ctl.p) {
+    CU(s->ws_ctl.ensure(2 * sizeof(int)));
+    CU(cudaMemset(s->ws_ctl.p, 0, 2 * sizeof(int)));
+  }
+  P.err = s->ws_ctl.as<int>() + 1;
+  return EP_OK;
 }
 
 // boundary accumulators: allocated, zero
@@ -231,6 +293,62 @@ int ensure_bacc(ep_schedule* s, int32_t R, cudaStream_t st) {
   return EP_OK;
 }
 
+// One forward step (edge kernel + shared-vertex fold) in schedule layout.
+int flux_step_any(ep_schedule* s, int32_t D, const float* w, const float* x_in, float* x_out,
+                  float* out, float tau, cudaStream_t st) {
+  ep::dev::FluxArgs a = flux_args(s, w, x_in, x_out, out, tau);
+  if (s->stages == 0) {
+    CU(ep::dev::flux_step(a, D, st));
+    return EP_OK;
+  }
+  ep::dev::TmaPlan P;
+  if (int rc = tma_plan(s, D, false, P)) return rc;
+  if (a.k > 0) {
+    struct Scope {
+      ep::dev::Timer* t;
+      cudaStream_t st;
+      Scope(ep::dev::Timer* t_, cudaStream_t s_) : t(t_), st(s_) {
+        if (t) t->begin(ep::dev::T_EDGE_FWD, st);
+      }
+      ~Scope() {
+        if (t) t->end(ep::dev::T_EDGE_FWD, st);
+      }
+    } sc(a.timer, st);
+    CU(ep::dev::flux_fwd_tma(a, P, D, st));
+  }
+  CU(ep::dev::bnd_update(a, D, x_out, x_in, out, st));
+  return EP_OK;
+}
+
+// One adjoint step in schedule layout.
+int flux_adj_any(ep_schedule* s, int32_t D, const float* w, const float* x, float* lam, float* gw,
+                 float tau, cudaStream_t st) {
+  ep::dev::FluxArgs a = flux_args(s, w, x, nullptr, nullptr, tau);
+  if (s->stages == 0) {
+    CU(ep::dev::flux_adjoint_step(a, D, lam, gw, st));
+    return EP_OK;
+  }
+  ep::dev::TmaPlan P;
+  if (int rc = tma_plan(s, D, true, P)) return rc;
+  if (a.k > 0) {
+    struct Scope {
+      ep::dev::Timer* t;
+      cudaStream_t st;
+      Scope(ep::dev::Timer* t_, cudaStream_t s_) : t(t_), st(s_) {
+        if (t) t->begin(ep::dev::T_EDGE_ADJ, st);
+      }
+      ~Scope() {
+        if (t) t->end(ep::dev::T_EDGE_ADJ, st);
+      }
+    } sc(a.timer, st);
+    CU(ep::dev::flux_adj_tma(a, P, D, lam, gw, st));
+  }
+  CU(ep::dev::bnd_update(a, D, lam, lam, nullptr, st));
+  return EP_OK;
+}
+
+bool misaligned(const void* p) { return p && ((uintptr_t)p & 15u); }
+
 int check_flux(ep_schedule* s, int32_t D) {
   if (!s) return fail(EP_EINVAL, "null schedule");
   if (bipartite(s)) return fail(EP_EINVAL, "flux kernels need a non-bipartite schedule");
@@ -242,9 +360,9 @@ int run_spmv(ep_schedule* s, const float* x, const float* w, float* y, cudaStrea
   const ep::HostSchedule& h = s->h;
   CU(s->ws_x.ensure((size_t)h.n * sizeof(float)));
   CU(s->ws_out.ensure((size_t)h.n * sizeof(float)));
-  CU(s->ws_w.ensure((size_t)h.m * sizeof(float)));
-  CU(ep::dev::layout_in(s->d_xrec.as<int32_t>(), h.n, 1, 1, x, s->ws_x.as<float>(), st, s->t()));
-  CU(ep::dev::gather(s->d_perm.as<int32_t>(), h.m, w, s->ws_w.as<float>(), st, s->t()));
+  CU(s->ws_w.ensure((size_t)wlen_of(s) * sizeof(float)));
+  CU(ep::dev::layout_in(s->d_xrec.as<int32_t>(), h.n, h.n, 1, x, s->ws_x.as<float>(), st, s->t()));
+  CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
   ep::dev::SpmvArgs a;
   a.desc = s->d_desc.as<ep::SpmvDesc>();
   a.k = h.k;
@@ -261,7 +379,7 @@ int run_spmv(ep_schedule* s, const float* x, const float* w, float* y, cudaStrea
   a.tpb = s->tpb;
   a.timer = s->t();
   CU(ep::dev::spmv(a, st));
-  CU(ep::dev::layout_out(s->d_yrec.as<int32_t>(), h.n, 1, 1, s->ws_out.as<float>(), y, st, s->t()));
+  CU(ep::dev::layout_out(s->d_yrec.as<int32_t>(), h.n, h.n, 1, s->ws_out.as<float>(), y, st, s->t()));
   return EP_OK;
 }
 
@@ -436,14 +554,21 @@ int32_t ep_record_floats(int32_t D) { return ep::record_floats(D); }
 
 int64_t ep_layout_floats(const ep_schedule* s, int32_t D) {
   if (!s) return fail(EP_EINVAL, "null schedule");
-  return bipartite(s) ? s->h.n : s->h.nd * ep::record_floats(D);
+  return bipartite(s) ? s->h.n : s->h.n_rec * ep::record_floats(D);
+}
+
+int64_t ep_weights_floats(const ep_schedule* s) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  return wlen_of(s);
 }
 
 int ep_layout_in(ep_schedule* s, int32_t D, const float* x, float* x_lay, void* stream) {
   g_error.clear();
   if (int rc = check_flux(s, D)) return rc;
+  if (!x || !x_lay) return fail(EP_EINVAL, "null argument");
+  if (misaligned(x_lay)) return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
-  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), s->h.nd, D, ep::record_floats(D), x, x_lay,
+  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), s->h.nd, s->h.n_rec, D, x, x_lay,
                         as_stream(stream), s->t()));
   return EP_OK;
 }
@@ -451,17 +576,20 @@ int ep_layout_in(ep_schedule* s, int32_t D, const float* x, float* x_lay, void* 
 int ep_layout_out(ep_schedule* s, int32_t D, const float* x_lay, float* x, void* stream) {
   g_error.clear();
   if (int rc = check_flux(s, D)) return rc;
+  if (!x || !x_lay) return fail(EP_EINVAL, "null argument");
+  if (misaligned(x_lay)) return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
-  CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), s->h.nd, D, ep::record_floats(D), x_lay, x,
+  CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), s->h.nd, s->h.n_rec, D, x_lay, x,
                          as_stream(stream), s->t()));
   return EP_OK;
 }
 
 int ep_weights_in(ep_schedule* s, const float* w, float* w_lay, void* stream) {
   g_error.clear();
-  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (!s || !w || !w_lay) return fail(EP_EINVAL, "null argument");
+  if (misaligned(w_lay)) return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
-  CU(ep::dev::gather(s->d_perm.as<int32_t>(), s->h.m, w, w_lay, as_stream(stream), s->t()));
+  CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, w_lay, as_stream(stream), s->t()));
   return EP_OK;
 }
 
@@ -469,7 +597,7 @@ int ep_weights_out_add(ep_schedule* s, const float* w_lay, float* w, void* strea
   g_error.clear();
   if (!s) return fail(EP_EINVAL, "null schedule");
   if (int rc = ensure_device(s)) return rc;
-  CU(ep::dev::scatter_add(s->d_perm.as<int32_t>(), s->h.m, w_lay, w, as_stream(stream), s->t()));
+  CU(ep::dev::scatter_add(wmap_of(s), wlen_of(s), w_lay, w, as_stream(stream), s->t()));
   return EP_OK;
 }
 
@@ -477,28 +605,36 @@ int ep_step(ep_schedule* s, int32_t D, const float* x_in, float* x_out, const fl
             float* out_lay, float tau, void* stream) {
   g_error.clear();
   if (int rc = check_flux(s, D)) return rc;
+  if (!x_in || !x_out || !w_lay) return fail(EP_EINVAL, "null argument");
+  if (misaligned(x_in) || misaligned(x_out) || misaligned(w_lay) || misaligned(out_lay))
+    return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
   cudaStream_t st = as_stream(stream);
   const int32_t R = ep::record_floats(D);
   if (int rc = ensure_bacc(s, R, st)) return rc;
-  if (out_lay && s->h.nd > s->h.n_int + s->h.n_bnd) {
-    const int64_t t = s->h.n_int + s->h.n_bnd;
-    CU(cudaMemsetAsync(out_lay + t * R, 0, (size_t)(s->h.nd - t) * R * sizeof(float), st));
+  if (out_lay && s->h.n_rec > s->h.n_int + s->h.n_bnd) {
+    // untouched records get a zero flux, plane by plane
+    const int64_t t = s->h.n_int + s->h.n_bnd, nr = s->h.n_rec;
+    int32_t first[4], width[4];
+    const int np = ep::planes_of(D, first, width);
+    for (int k = 0; k < np; ++k)
+      CU(cudaMemsetAsync(out_lay + first[k] * nr + t * width[k], 0,
+                         (size_t)(nr - t) * width[k] * sizeof(float), st));
   }
-  CU(ep::dev::flux_step(flux_args(s, w_lay, x_in, x_out, out_lay, tau), D, st));
-  return EP_OK;
+  return flux_step_any(s, D, w_lay, x_in, x_out, out_lay, tau, st);
 }
 
 int ep_adjoint_step(ep_schedule* s, int32_t D, const float* x_lay, const float* w_lay, float* lam,
                     float* grad_w_lay, float tau, void* stream) {
   g_error.clear();
   if (int rc = check_flux(s, D)) return rc;
+  if (!x_lay || !w_lay || !lam || !grad_w_lay) return fail(EP_EINVAL, "null argument");
+  if (misaligned(x_lay) || misaligned(w_lay) || misaligned(lam) || misaligned(grad_w_lay))
+    return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
   cudaStream_t st = as_stream(stream);
   if (int rc = ensure_bacc(s, ep::record_floats(D), st)) return rc;
-  CU(ep::dev::flux_adjoint_step(flux_args(s, w_lay, x_lay, nullptr, nullptr, tau), D, lam,
-                                grad_w_lay, st));
-  return EP_OK;
+  return flux_adj_any(s, D, w_lay, x_lay, lam, grad_w_lay, tau, st);
 }
 
 int ep_run(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out, int32_t D,
@@ -520,24 +656,24 @@ int ep_run(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out,
   if (int rc = ensure_device(s)) return rc;
   const ep::HostSchedule& h = s->h;
   const int32_t R = ep::record_floats(D);
-  const size_t lay = (size_t)h.nd * R * sizeof(float);
+  const size_t lay = (size_t)h.n_rec * R * sizeof(float);
   CU(s->ws_x.ensure(lay));
-  CU(s->ws_w.ensure((size_t)h.m * sizeof(float)));
+  CU(s->ws_w.ensure((size_t)wlen_of(s) * sizeof(float)));
   if (out) {
     CU(s->ws_out.ensure(lay));
   }
   if (int rc = ensure_bacc(s, R, st)) return rc;
-  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, D, R, x, s->ws_x.as<float>(), st, s->t()));
-  CU(ep::dev::gather(s->d_perm.as<int32_t>(), h.m, w, s->ws_w.as<float>(), st, s->t()));
+  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, x, s->ws_x.as<float>(), st, s->t()));
+  CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
   if (out) CU(cudaMemsetAsync(s->ws_out.p, 0, lay, st));
   for (int32_t t = 0; t < steps; ++t) {
     float* o = (out && t == steps - 1) ? s->ws_out.as<float>() : nullptr;
-    CU(ep::dev::flux_step(flux_args(s, s->ws_w.as<float>(), s->ws_x.as<float>(),
-                                    s->ws_x.as<float>(), o, tau),
-                          D, st));
+    if (int rc = flux_step_any(s, D, s->ws_w.as<float>(), s->ws_x.as<float>(), s->ws_x.as<float>(), o,
+                               tau, st))
+      return rc;
   }
-  CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, D, R, s->ws_x.as<float>(), x, st, s->t()));
-  if (out) CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, D, R, s->ws_out.as<float>(), out, st, s->t()));
+  CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, s->ws_x.as<float>(), x, st, s->t()));
+  if (out) CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, s->ws_out.as<float>(), out, st, s->t()));
   return EP_OK;
 }
 
@@ -574,25 +710,27 @@ int ep_run_adjoint(ep_schedule* s, const float* x0, const float* w, float* lam, 
   cudaStream_t st = as_stream(stream);
   const ep::HostSchedule& h = s->h;
   const int32_t R = ep::record_floats(D);
-  const size_t lay = (size_t)h.nd * R;
+  const size_t lay = (size_t)h.n_rec * R;
   CU(s->ws_hist.ensure(lay * steps * sizeof(float)));
   CU(s->ws_lam.ensure(lay * sizeof(float)));
-  CU(s->ws_w.ensure((size_t)h.m * sizeof(float)));
-  CU(s->ws_gw.ensure((size_t)h.m * sizeof(float)));
+  CU(s->ws_w.ensure((size_t)wlen_of(s) * sizeof(float)));
+  CU(s->ws_gw.ensure((size_t)wlen_of(s) * sizeof(float)));
   if (int rc = ensure_bacc(s, R, st)) return rc;
   float* hist = s->ws_hist.as<float>();
-  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, D, R, x0, hist, st, s->t()));
-  CU(ep::dev::gather(s->d_perm.as<int32_t>(), h.m, w, s->ws_w.as<float>(), st, s->t()));
-  CU(cudaMemsetAsync(s->ws_gw.p, 0, (size_t)h.m * sizeof(float), st));
+  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, x0, hist, st, s->t()));
+  CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
+  CU(cudaMemsetAsync(s->ws_gw.p, 0, (size_t)wlen_of(s) * sizeof(float), st));
   for (int32_t t = 0; t + 1 < steps; ++t)
-    CU(ep::dev::flux_step(
-        flux_args(s, s->ws_w.as<float>(), hist + lay * t, hist + lay * (t + 1), nullptr, tau), D, st));
-  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, D, R, lam, s->ws_lam.as<float>(), st, s->t()));
+    if (int rc = flux_step_any(s, D, s->ws_w.as<float>(), hist + lay * t, hist + lay * (t + 1), nullptr,
+                               tau, st))
+      return rc;
+  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, lam, s->ws_lam.as<float>(), st, s->t()));
   for (int32_t t = steps - 1; t >= 0; --t)
-    CU(ep::dev::flux_adjoint_step(flux_args(s, s->ws_w.as<float>(), hist + lay * t, nullptr, nullptr, tau),
-                                  D, s->ws_lam.as<float>(), s->ws_gw.as<float>(), st));
-  CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, D, R, s->ws_lam.as<float>(), lam, st, s->t()));
-  CU(ep::dev::scatter_add(s->d_perm.as<int32_t>(), h.m, s->ws_gw.as<float>(), grad_w, st, s->t()));
+    if (int rc = flux_adj_any(s, D, s->ws_w.as<float>(), hist + lay * t, s->ws_lam.as<float>(),
+                              s->ws_gw.as<float>(), tau, st))
+      return rc;
+  CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, s->ws_lam.as<float>(), lam, st, s->t()));
+  CU(ep::dev::scatter_add(wmap_of(s), wlen_of(s), s->ws_gw.as<float>(), grad_w, st, s->t()));
   return EP_OK;
 }
 
@@ -609,6 +747,33 @@ int ep_timing_read(ep_schedule* s, int32_t kernel_class, double* total_ms, int64
   s->timer.collect();
   if (total_ms) *total_ms = s->timer.total[kernel_class];
   if (launches) *launches = s->timer.count[kernel_class];
+  return EP_OK;
+}
+
+int ep_set_pipeline(ep_schedule* s, int32_t stages, int32_t ahead) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (stages < 0 || stages == 1 || stages > ep::dev::kMaxStages)
+    return fail(EP_EINVAL, "stages = %d (0, or 2..%d)", stages, ep::dev::kMaxStages);
+  if (ahead < 0 || ahead > 64) return fail(EP_EINVAL, "ahead = %d (0..64)", ahead);
+  s->stages = stages;
+  s->ahead = ahead;
+  return EP_OK;
+}
+
+int ep_check_errors(ep_schedule* s, int32_t* code, void* stream) {
+  g_error.clear();
+  if (!s || !code) return fail(EP_EINVAL, "null argument");
+  *code = 0;
+  if (!s->ws_ctl.p) return EP_OK;
+  int v[2] = {0, 0};
+  cudaStream_t st = as_stream(stream);
+  CU(cudaMemcpyAsync(v, s->ws_ctl.p, sizeof v, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  *code = v[1];
+  if (v[1]) {
+    CU(cudaMemsetAsync(s->ws_ctl.as<int>() + 1, 0, sizeof(int), st));
+    return fail(EP_ETIMEOUT, "a pipelined kernel gave up waiting (code %d)", v[1]);
+  }
   return EP_OK;
 }
 

@@ -8,20 +8,36 @@
 
 namespace ep {
 
-// Flux kernels: one descriptor per schedule block.  A block's local slots are
-//   [0, n_int)                  records used by this block only (p_v = 1),
-//                               contiguous from int_lo;
-//   [n_int, n_int + n_ob)       records first touched by this block and used
-//                               by later blocks too, contiguous from bnd_lo;
-//   [n_int + n_ob, ... + nf)    records owned by earlier blocks, listed in
-//                               flist[f0 .. f0 + nf).
+// Flux kernels: one descriptor per schedule block.  The block's vertices sit
+// at shared-memory positions
+//   [pi, pi + n_int)   records used by this block only (p_v = 1), contiguous
+//                      from int_lo;
+//   [pb, pb + n_ob)    records first touched by this block and used by later
+//                      blocks too, contiguous from bnd_lo;
+//   [pf, pf + nf)      records owned by earlier blocks, flist[f0 .. f0 + nf);
+// with pi = int_lo mod 4 and pb = bnd_lo mod 4 (mod 4), so that a 16-byte
+// aligned run of records in a state plane maps to a 16-byte aligned run in
+// shared memory.  Positions outside the three runs are unused.  Every
+// position p in [0, np) has the incidence entries inc[i0 + ptr[q0 + p] ..
+// i0 + ptr[q0 + p + 1]): (other position) | (task << 15) | (p is src << 31).
+// The task weights of the block are w_lay[w0 .. w0 + ne).  Every per-block
+// segment (entries, offsets, foreign ids, weights) starts on a 16-byte
+// boundary and is zero-padded to a multiple of 16 bytes, so it can be moved
+// with one bulk copy.
 struct FluxDesc {
-  int32_t e0, ne;
+  int32_t w0, ne;        // task weights w_lay[w0, w0 + ne)
   int32_t int_lo, n_int;
   int32_t bnd_lo, n_ob;
   int32_t f0, nf;
+  int32_t pi, pb, pf, np;
+  int32_t i0, q0, nent, pad;
 };
-static_assert(sizeof(FluxDesc) == 32, "FluxDesc layout");
+static_assert(sizeof(FluxDesc) == 64, "FluxDesc layout");
+
+// Incidence entry fields
+constexpr uint32_t kPosMask = 0x7fffu;
+constexpr int kTaskShift = 15;
+constexpr uint32_t kSrcBit = 0x80000000u;
 
 // SpMV kernels (bipartite): x records are read only, y records accumulate.
 //   x slots: [0, n_xo) contiguous from x_lo, then n_xf from xlist[fx0..]
@@ -48,12 +64,19 @@ struct HostSchedule {
   int32_t max_ne = 0;
 
   // flux layout (non-bipartite)
+  int64_t n_rec = 0;        // records per state plane: nd rounded up to a multiple of 4
   int64_t n_int = 0;        // records [0, n_int) are single-block vertices
   int64_t n_bnd = 0;        // records [n_int, n_int + n_bnd) are shared
   std::vector<int32_t> rec_of;  // data vertex -> record (all nd vertices)
   std::vector<FluxDesc> fdesc;
   std::vector<int32_t> flist;
-  int32_t max_nv = 0;
+  std::vector<uint32_t> inc;   // incidence entries (flux)
+  std::vector<uint16_t> ptr;   // per-position entry offsets within a block (flux)
+  int32_t max_nv = 0;          // max positions per block
+  int32_t max_nent = 0;        // max incidence entries per block
+  int32_t max_nf = 0;          // max foreign records per block
+  int64_t w_pad = 0;           // length of the padded weight layout
+  std::vector<int32_t> wmap;   // weight slot -> task id (-1 for padding)
 
   // spmv layout (bipartite): x records 0..n-1, y records 0..n-1
   int64_t ny_int = 0, ny_bnd = 0;
@@ -73,8 +96,17 @@ void partition_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t 
 // cpack, cost, kernel layout).  Returns an empty string or an error message.
 std::string build_schedule(HostSchedule& s, int threads);
 
-inline int32_t record_floats(int32_t D) {
-  return D <= 1 ? 1 : D <= 2 ? 2 : D <= 4 ? 4 : 8;
+// State layout: the D components of a record are split into planes of
+// width 4, 2 and 1 (D = 4a + 2b + c); plane k holds n_rec records of its
+// width contiguously, so a state buffer is n_rec * D floats without padding.
+inline int32_t record_floats(int32_t D) { return D; }
+// planes of a D-wide record: count, first component and width of each
+inline int planes_of(int32_t D, int32_t first[4], int32_t width[4]) {
+  int np = 0, c = 0;
+  for (int i = 0; i < D / 4; ++i, c += 4) first[np] = c, width[np++] = 4;
+  if (D % 4 >= 2) first[np] = c, width[np++] = 2, c += 2;
+  if (D % 2) first[np] = c, width[np++] = 1;
+  return np;
 }
 
 }  // namespace ep

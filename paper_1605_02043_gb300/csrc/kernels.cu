@@ -33,198 +33,274 @@ struct VecOf<4> {
   using T = float4;
 };
 
-// a record of R floats is R/V chunks of a V-wide vector
-template <int R>
-struct Rec {
-  static constexpr int V = R >= 4 ? 4 : R;
-  static constexpr int NC = R / V;
-  using T = typename VecOf<V>::T;
+// The D components of a record live in planes of width 4, 2 and 1
+// (D = 4a + 2b + c).  Plane k starts at component first(k): in a buffer of
+// n records it is the float range [first(k) * n, (first(k) + width(k)) * n).
+template <int D>
+struct Planes {
+  static constexpr int A = D / 4, B = (D % 4) / 2, C1 = D % 2;
+  static constexpr int NP = A + B + C1;
+  __host__ __device__ static constexpr int width(int k) { return k < A ? 4 : (k < A + B ? 2 : 1); }
+  __host__ __device__ static constexpr int first(int k) {
+    return k < A ? 4 * k : (k < A + B ? 4 * A + 2 * (k - A) : 4 * A + 2 * B);
+  }
 };
 
-__device__ __forceinline__ float lane(const float& v, int) { return v; }
-__device__ __forceinline__ float lane(const float2& v, int i) { return i == 0 ? v.x : v.y; }
-__device__ __forceinline__ float lane(const float4& v, int i) {
-  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
-}
-__device__ __forceinline__ float axpy(float a, float x, float y) { return fmaf(a, x, y); }
-__device__ __forceinline__ float2 axpy(float a, float2 x, float2 y) {
-  return make_float2(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y));
-}
-__device__ __forceinline__ float4 axpy(float a, float4 x, float4 y) {
-  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
-}
-template <typename T>
-__device__ __forceinline__ T zero_of();
-template <>
-__device__ __forceinline__ float zero_of<float>() { return 0.f; }
-template <>
-__device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.f, 0.f); }
-template <>
-__device__ __forceinline__ float4 zero_of<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-
-// Global accumulation of lanes [c*V, c*V+V) of a record, only lanes < D.
-template <int D, int V>
-__device__ __forceinline__ void red_chunk(float* dst, int c, const typename VecOf<V>::T& a) {
-  if (c * V + V <= D) {
-    if constexpr (V == 4)
-      atomicAdd(reinterpret_cast<float4*>(dst), a);
-    else if constexpr (V == 2)
-      atomicAdd(reinterpret_cast<float2*>(dst), a);
-    else
-      atomicAdd(dst, lane(a, 0));
+template <int W>
+__device__ __forceinline__ void vload(const float* p, float* v) {
+  if constexpr (W == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  } else if constexpr (W == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x, v[1] = t.y;
   } else {
-#pragma unroll
-    for (int l = 0; l < V; ++l)
-      if (c * V + l < D) atomicAdd(dst + l, lane(a, l));
+    v[0] = *p;
+  }
+}
+template <int W>
+__device__ __forceinline__ void vload_g(const float* __restrict__ p, float* v) {
+  if constexpr (W == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  } else if constexpr (W == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x, v[1] = t.y;
+  } else {
+    v[0] = __ldg(p);
+  }
+}
+template <int W>
+__device__ __forceinline__ void vstore(float* p, const float* v) {
+  if constexpr (W == 4)
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else if constexpr (W == 2)
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  else
+    *p = v[0];
+}
+template <int W>
+__device__ __forceinline__ void vred(float* p, const float* v) {
+  if constexpr (W == 4)
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  else if constexpr (W == 2)
+    atomicAdd(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+  else
+    atomicAdd(p, v[0]);
+}
+
+// Record r of a planar buffer of n records <-> registers v[0..D), one vector
+// access per plane (planes unrolled at compile time).
+template <int D, bool GLOBAL, int K = 0>
+__device__ __forceinline__ void rec_load(const float* base, int64_t n, int64_t r, float* v) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    const float* q = base + F * n + r * W;
+    if constexpr (GLOBAL)
+      vload_g<W>(q, v + F);
+    else
+      vload<W>(q, v + F);
+    rec_load<D, GLOBAL, K + 1>(base, n, r, v);
+  }
+}
+template <int D, int K = 0>
+__device__ __forceinline__ void rec_store(float* base, int64_t n, int64_t r, const float* v) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    vstore<W>(base + F * n + r * W, v + F);
+    rec_store<D, K + 1>(base, n, r, v);
+  }
+}
+template <int D, int K = 0>
+__device__ __forceinline__ void rec_red(float* base, int64_t n, int64_t r, const float* v) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    vred<W>(base + F * n + r * W, v + F);
+    rec_red<D, K + 1>(base, n, r, v);
   }
 }
 
-// record id of local slot `slot` in a flux block
+// record at shared position p of a flux block, -1 for an unused position
 __device__ __forceinline__ int32_t flux_rec(const FluxDesc& d, const int32_t* __restrict__ flist,
-                                            int slot) {
-  const int own = d.n_int + d.n_ob;
-  return slot < d.n_int ? d.int_lo + slot
-         : slot < own   ? d.bnd_lo + (slot - d.n_int)
-                        : __ldg(flist + d.f0 + (slot - own));
+                                            int p) {
+  if (p >= d.pi && p < d.pi + d.n_int) return d.int_lo + (p - d.pi);
+  if (p >= d.pb && p < d.pb + d.n_ob) return d.bnd_lo + (p - d.pb);
+  if (p >= d.pf && p < d.pf + d.nf) return __ldg(flist + d.f0 + (p - d.pf));
+  return -1;
+}
+
+// Shared-memory carve-up of a flux block: planes of npos positions each
+// (npos a multiple of 4 keeps every plane 16-byte aligned), then weights,
+// incidence entries and position offsets.
+struct FluxSmem {
+  float* x;
+  float* lam;
+  float* w;
+  uint32_t* ent;
+  uint16_t* ptr;
+  int npos;
+};
+template <int D>
+__device__ __forceinline__ FluxSmem flux_smem(const FluxDesc& d, bool with_lam) {
+  extern __shared__ float4 smem4[];
+  FluxSmem s;
+  s.npos = (d.np + 3) & ~3;
+  s.x = reinterpret_cast<float*>(smem4);
+  s.lam = s.x + D * s.npos;
+  s.w = with_lam ? s.lam + D * s.npos : s.lam;
+  s.ent = reinterpret_cast<uint32_t*>(s.w + d.ne);
+  s.ptr = reinterpret_cast<uint16_t*>(s.ent + d.nent);
+  return s;
+}
+
+template <int D>
+__device__ __forceinline__ void stage_block(const FluxDesc& d, const FluxSmem& s,
+                                            const int32_t* __restrict__ flist,
+                                            const uint32_t* __restrict__ inc,
+                                            const uint16_t* __restrict__ ptr,
+                                            const float* __restrict__ w, const float* x, int64_t n_rec,
+                                            const float* lam) {
+  // independent loads first, so no warp waits on a foreign id before issuing them
+  for (int i = threadIdx.x; i < d.ne; i += blockDim.x) s.w[i] = __ldg(w + d.w0 + i);
+  for (int i = threadIdx.x; i < d.nent; i += blockDim.x) s.ent[i] = __ldg(inc + d.i0 + i);
+  for (int i = threadIdx.x; i <= d.np; i += blockDim.x) s.ptr[i] = __ldg(ptr + d.q0 + i);
+  for (int p = threadIdx.x; p < d.np; p += blockDim.x) {
+    const int32_t r = flux_rec(d, flist, p);
+    if (r < 0) continue;
+    float v[D];
+    rec_load<D, true>(x, n_rec, r, v);
+    rec_store<D>(s.x, s.npos, p, v);
+    if (lam) {
+      rec_load<D, false>(lam, n_rec, r, v);
+      rec_store<D>(s.lam, s.npos, p, v);
+    }
+  }
 }
 
 // ------------------------------------------------------------- flux forward
 
-template <int D, int R>
-__global__ void flux_fwd_kernel(const FluxDesc* __restrict__ desc, const int32_t* __restrict__ flist,
-                                const uint32_t* __restrict__ loc, const float* __restrict__ w,
-                                const float* __restrict__ x_in, float* __restrict__ x_out,
-                                float* __restrict__ bacc, float* __restrict__ out, int32_t n_int,
-                                float tau) {
-  using RT = Rec<R>;
-  using T = typename RT::T;
-  extern __shared__ float4 smem4[];
+// One CUDA block per schedule block.  After staging, the thread of position p
+// sums the flux of every task at p over p's incidence list, reading the other
+// endpoint from shared memory: d = x_o - x_p, f = w d / (1 + |d|^2).  The
+// difference is exactly antisymmetric in IEEE arithmetic, so both endpoints of
+// a task see +f and -f of the same value.
+template <int D>
+__global__ void __launch_bounds__(1024) flux_fwd_kernel(
+    const FluxDesc* __restrict__ desc, const int32_t* __restrict__ flist,
+    const uint32_t* __restrict__ inc, const uint16_t* __restrict__ ptr, const float* __restrict__ w,
+    const float* x_in, float* x_out, float* __restrict__ bacc, float* __restrict__ out,
+    int64_t n_rec, int64_t n_int, int64_t n_bnd, float tau) {
   const FluxDesc d = desc[blockIdx.x];
-  const int nv = d.n_int + d.n_ob + d.nf;
-  float* xs = reinterpret_cast<float*>(smem4);
-  float* acc = xs + (size_t)nv * R;
-  for (int i = threadIdx.x; i < nv * RT::NC; i += blockDim.x) {
-    const int slot = i / RT::NC, c = i % RT::NC;
-    const int32_t r = flux_rec(d, flist, slot);
-    reinterpret_cast<T*>(xs + slot * R)[c] =
-        __ldg(reinterpret_cast<const T*>(x_in + (size_t)r * R) + c);
-    reinterpret_cast<T*>(acc + slot * R)[c] = zero_of<T>();
-  }
+  const FluxSmem s = flux_smem<D>(d, false);
+  stage_block<D>(d, s, flist, inc, ptr, w, x_in, n_rec, nullptr);
   __syncthreads();
-  for (int j = threadIdx.x; j < d.ne; j += blockDim.x) {
-    const uint32_t p = __ldg(loc + d.e0 + j);
-    const int u = (int)(p & 0xffffu), v = (int)(p >> 16);
-    const float we = __ldg(w + d.e0 + j);
-    float dd[D];
-    float s = 0.f;
+  for (int p = threadIdx.x; p < d.np; p += blockDim.x) {
+    const int k0 = s.ptr[p], k1 = s.ptr[p + 1];
+    if (k0 == k1) continue;  // unused position
+    float xp[D], acc[D];
+    rec_load<D, false>(s.x, s.npos, p, xp);
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      dd[c] = xs[v * R + c] - xs[u * R + c];
-      s = fmaf(dd[c], dd[c], s);
-    }
-    const float coef = we / (1.f + s);
+    for (int c = 0; c < D; ++c) acc[c] = 0.f;
+    for (int k = k0; k < k1; ++k) {
+      const uint32_t e = s.ent[k];
+      float xo[D];
+      rec_load<D, false>(s.x, s.npos, (int)(e & kPosMask), xo);
+      float dd[D], q = 0.f;
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const float f = coef * dd[c];
-      atomicAdd(acc + u * R + c, f);
-      atomicAdd(acc + v * R + c, -f);
+      for (int c = 0; c < D; ++c) {
+        dd[c] = xo[c] - xp[c];
+        q = fmaf(dd[c], dd[c], q);
+      }
+      const float coef = __fdividef(s.w[(e >> kTaskShift) & 0xffffu], 1.f + q);
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c] = fmaf(coef, dd[c], acc[c]);
     }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nv * RT::NC; i += blockDim.x) {
-    const int slot = i / RT::NC, c = i % RT::NC;
-    const T a = reinterpret_cast<const T*>(acc + slot * R)[c];
-    if (slot < d.n_int) {
-      const int32_t r = d.int_lo + slot;
-      const T xv = reinterpret_cast<const T*>(xs + slot * R)[c];
-      reinterpret_cast<T*>(x_out + (size_t)r * R)[c] = axpy(tau, a, xv);
-      if (out) reinterpret_cast<T*>(out + (size_t)r * R)[c] = a;
+    const int32_t r = flux_rec(d, flist, p);
+    if (p < d.pi + d.n_int) {
+      float xn[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) xn[c] = fmaf(tau, acc[c], xp[c]);
+      rec_store<D>(x_out, n_rec, r, xn);
+      if (out) rec_store<D>(out, n_rec, r, acc);
     } else {
-      const int32_t r = flux_rec(d, flist, slot);
-      red_chunk<D, RT::V>(bacc + (size_t)(r - n_int) * R + c * RT::V, c, a);
+      rec_red<D>(bacc, n_bnd, r - n_int, acc);
     }
   }
 }
 
-// shared records: x_out = x_in + tau * acc; out = acc; acc = 0
-template <int R>
-__global__ void bnd_update_kernel(const float* __restrict__ x_in, float* __restrict__ x_out,
-                                  float* __restrict__ bacc, float* __restrict__ out, int64_t n_int,
+// shared records: x_out = x_in + tau * acc; out = acc; acc = 0 (plane by plane)
+template <int D>
+__global__ void bnd_update_kernel(const float* x_in, float* x_out, float* __restrict__ bacc,
+                                  float* __restrict__ out, int64_t n_rec, int64_t n_int,
                                   int64_t n_bnd, float tau) {
-  using RT = Rec<R>;
-  using T = typename RT::T;
-  const int64_t total = n_bnd * RT::NC;
-  const T* xi = reinterpret_cast<const T*>(x_in + (size_t)n_int * R);
-  T* xo = reinterpret_cast<T*>(x_out + (size_t)n_int * R);
-  T* ba = reinterpret_cast<T*>(bacc);
-  T* oo = out ? reinterpret_cast<T*>(out + (size_t)n_int * R) : nullptr;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bnd;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const T a = ba[i];
-    xo[i] = axpy(tau, a, xi[i]);
-    if (oo) oo[i] = a;
-    ba[i] = zero_of<T>();
+    float a[D], x[D];
+    rec_load<D, false>(bacc, n_bnd, i, a);
+    rec_load<D, false>(x_in, n_rec, n_int + i, x);
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = fmaf(tau, a[c], x[c]);
+    rec_store<D>(x_out, n_rec, n_int + i, x);
+    if (out) rec_store<D>(out, n_rec, n_int + i, a);
+#pragma unroll
+    for (int c = 0; c < D; ++c) a[c] = 0.f;
+    rec_store<D>(bacc, n_bnd, i, a);
   }
 }
 
 // ------------------------------------------------------------- flux adjoint
 
-template <int D, int R>
-__global__ void flux_adj_kernel(const FluxDesc* __restrict__ desc, const int32_t* __restrict__ flist,
-                                const uint32_t* __restrict__ loc, const float* __restrict__ w,
-                                const float* __restrict__ x, float* __restrict__ lam,
-                                float* __restrict__ gw, float* __restrict__ bacc, int32_t n_int,
-                                float tau) {
-  using RT = Rec<R>;
-  using T = typename RT::T;
-  extern __shared__ float4 smem4[];
+// Reverse step: at position p with other endpoint o of a task,
+// d = x_o - x_p, g = lam_p - lam_o, q = |d|^2,
+// contribution to lam_p: -w (g/(1+q) - 2 d (d.g)/(1+q)^2), and the src-side
+// entry adds tau (d.g)/(1+q) to the task's weight gradient.
+template <int D>
+__global__ void __launch_bounds__(1024) flux_adj_kernel(
+    const FluxDesc* __restrict__ desc, const int32_t* __restrict__ flist,
+    const uint32_t* __restrict__ inc, const uint16_t* __restrict__ ptr, const float* __restrict__ w,
+    const float* __restrict__ x, float* lam, float* __restrict__ gw, float* __restrict__ bacc,
+    int64_t n_rec, int64_t n_int, int64_t n_bnd, float tau) {
   const FluxDesc d = desc[blockIdx.x];
-  const int nv = d.n_int + d.n_ob + d.nf;
-  float* xs = reinterpret_cast<float*>(smem4);
-  float* ls = xs + (size_t)nv * R;
-  float* acc = ls + (size_t)nv * R;
-  for (int i = threadIdx.x; i < nv * RT::NC; i += blockDim.x) {
-    const int slot = i / RT::NC, c = i % RT::NC;
-    const int32_t r = flux_rec(d, flist, slot);
-    reinterpret_cast<T*>(xs + slot * R)[c] = __ldg(reinterpret_cast<const T*>(x + (size_t)r * R) + c);
-    reinterpret_cast<T*>(ls + slot * R)[c] = reinterpret_cast<const T*>(lam + (size_t)r * R)[c];
-    reinterpret_cast<T*>(acc + slot * R)[c] = zero_of<T>();
-  }
+  const FluxSmem s = flux_smem<D>(d, true);
+  stage_block<D>(d, s, flist, inc, ptr, w, x, n_rec, lam);
   __syncthreads();
-  for (int j = threadIdx.x; j < d.ne; j += blockDim.x) {
-    const uint32_t p = __ldg(loc + d.e0 + j);
-    const int u = (int)(p & 0xffffu), v = (int)(p >> 16);
-    const float we = __ldg(w + d.e0 + j);
-    float dd[D], gb[D];
-    float s = 0.f, dg = 0.f;
+  for (int p = threadIdx.x; p < d.np; p += blockDim.x) {
+    const int k0 = s.ptr[p], k1 = s.ptr[p + 1];
+    if (k0 == k1) continue;
+    float xp[D], lp[D], acc[D];
+    rec_load<D, false>(s.x, s.npos, p, xp);
+    rec_load<D, false>(s.lam, s.npos, p, lp);
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      dd[c] = xs[v * R + c] - xs[u * R + c];
-      gb[c] = ls[u * R + c] - ls[v * R + c];
-      s = fmaf(dd[c], dd[c], s);
-      dg = fmaf(dd[c], gb[c], dg);
-    }
-    const float inv = 1.f / (1.f + s);
-    gw[d.e0 + j] += tau * dg * inv;
-    const float two = 2.f * dg * inv * inv;
+    for (int c = 0; c < D; ++c) acc[c] = 0.f;
+    for (int k = k0; k < k1; ++k) {
+      const uint32_t e = s.ent[k];
+      const int o = (int)(e & kPosMask);
+      const int t = (int)((e >> kTaskShift) & 0xffffu);
+      float xo[D], lo[D];
+      rec_load<D, false>(s.x, s.npos, o, xo);
+      rec_load<D, false>(s.lam, s.npos, o, lo);
+      float dd[D], g[D], q = 0.f, dg = 0.f;
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const float h = we * (gb[c] * inv - two * dd[c]);
-      atomicAdd(acc + v * R + c, h);
-      atomicAdd(acc + u * R + c, -h);
+      for (int c = 0; c < D; ++c) {
+        dd[c] = xo[c] - xp[c];
+        g[c] = lp[c] - lo[c];
+        q = fmaf(dd[c], dd[c], q);
+        dg = fmaf(dd[c], g[c], dg);
+      }
+      const float inv = __fdividef(1.f, 1.f + q);
+      const float we = s.w[t];
+      const float two = 2.f * dg * inv * inv;
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c] -= we * (g[c] * inv - two * dd[c]);
+      if (e & kSrcBit) gw[d.w0 + t] += tau * dg * inv;
     }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nv * RT::NC; i += blockDim.x) {
-    const int slot = i / RT::NC, c = i % RT::NC;
-    const T a = reinterpret_cast<const T*>(acc + slot * R)[c];
-    if (slot < d.n_int) {
-      const int32_t r = d.int_lo + slot;
-      const T lv = reinterpret_cast<const T*>(ls + slot * R)[c];
-      reinterpret_cast<T*>(lam + (size_t)r * R)[c] = axpy(tau, a, lv);
+    const int32_t r = flux_rec(d, flist, p);
+    if (p < d.pi + d.n_int) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) lp[c] = fmaf(tau, acc[c], lp[c]);
+      rec_store<D>(lam, n_rec, r, lp);
     } else {
-      const int32_t r = flux_rec(d, flist, slot);
-      red_chunk<D, RT::V>(bacc + (size_t)(r - n_int) * R + c * RT::V, c, a);
+      rec_red<D>(bacc, n_bnd, r - n_int, acc);
     }
   }
 }
@@ -262,36 +338,28 @@ __global__ void spmv_kernel(const SpmvDesc* __restrict__ desc, const int32_t* __
 
 // ------------------------------------------------------------------- layout
 
-template <int R>
-__global__ void layout_in_kernel(const int32_t* __restrict__ rec_of, int64_t n, int D,
+// caller layout [D][n] (by data vertex) <-> planar records (by record id)
+template <int D>
+__global__ void layout_in_kernel(const int32_t* __restrict__ rec_of, int64_t n, int64_t n_rec,
                                  const float* __restrict__ x, float* __restrict__ x_lay) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
-    float t[R];
+    float t[D];
 #pragma unroll
-    for (int c = 0; c < R; ++c) t[c] = c < D ? x[(size_t)c * n + v] : 0.f;
-    using RT = Rec<R>;
-    using T = typename RT::T;
-    T* dst = reinterpret_cast<T*>(x_lay + (size_t)rec_of[v] * R);
-#pragma unroll
-    for (int c = 0; c < RT::NC; ++c) dst[c] = reinterpret_cast<const T*>(t)[c];
+    for (int c = 0; c < D; ++c) t[c] = __ldg(x + (size_t)c * n + v);
+    rec_store<D>(x_lay, n_rec, __ldg(rec_of + v), t);
   }
 }
 
-template <int R>
-__global__ void layout_out_kernel(const int32_t* __restrict__ rec_of, int64_t n, int D,
+template <int D>
+__global__ void layout_out_kernel(const int32_t* __restrict__ rec_of, int64_t n, int64_t n_rec,
                                   const float* __restrict__ x_lay, float* __restrict__ x) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
-    using RT = Rec<R>;
-    using T = typename RT::T;
-    float t[R];
-    const T* src = reinterpret_cast<const T*>(x_lay + (size_t)rec_of[v] * R);
+    float t[D];
+    rec_load<D, true>(x_lay, n_rec, __ldg(rec_of + v), t);
 #pragma unroll
-    for (int c = 0; c < RT::NC; ++c) reinterpret_cast<T*>(t)[c] = src[c];
-#pragma unroll
-    for (int c = 0; c < R; ++c)
-      if (c < D) x[(size_t)c * n + v] = t[c];
+    for (int c = 0; c < D; ++c) x[(size_t)c * n + v] = t[c];
   }
 }
 
@@ -299,14 +367,20 @@ __global__ void gather_kernel(const int32_t* __restrict__ perm, int64_t m, const
                               float* __restrict__ w_lay) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
-    w_lay[i] = __ldg(w + perm[i]);
+  {
+    const int32_t t = perm[i];
+    w_lay[i] = t >= 0 ? __ldg(w + t) : 0.f;
+  }
 }
 
 __global__ void scatter_add_kernel(const int32_t* __restrict__ perm, int64_t m,
                                    const float* __restrict__ w_lay, float* __restrict__ w) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
-    w[perm[i]] += w_lay[i];
+  {
+    const int32_t t = perm[i];
+    if (t >= 0) w[t] += w_lay[i];
+  }
 }
 
 // --------------------------------------------------------------------- cost
@@ -391,38 +465,46 @@ struct Scope {
   }
 };
 
-template <int D, int R>
+size_t flux_smem_bytes(const FluxArgs& a, int D, int copies) {
+  const size_t npos = ((size_t)a.max_np + 3) & ~(size_t)3;
+  return (size_t)copies * D * npos * sizeof(float) + (size_t)a.max_ne * sizeof(float) +
+         (size_t)a.max_nent * sizeof(uint32_t) + ((size_t)a.max_np + 1) * sizeof(uint16_t) + 16;
+}
+
+template <int D>
 cudaError_t flux_step_t(const FluxArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)a.max_nv * R * sizeof(float) * 2;
-  cudaError_t e = allow_smem(flux_fwd_kernel<D, R>, smem);
+  const size_t smem = flux_smem_bytes(a, D, 1);
+  cudaError_t e = allow_smem(flux_fwd_kernel<D>, smem);
   if (e != cudaSuccess) return e;
   if (a.k > 0) {
     Scope sc(a.timer, T_EDGE_FWD, st);
-    flux_fwd_kernel<D, R><<<(unsigned)a.k, a.tpb, smem, st>>>(
-        a.desc, a.flist, a.loc, a.w, a.x_in, a.x_out, a.bacc, a.out, (int32_t)a.n_int, a.tau);
+    flux_fwd_kernel<D><<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w, a.x_in,
+                                                          a.x_out, a.bacc, a.out, a.n_rec, a.n_int,
+                                                          a.n_bnd, a.tau);
   }
   if (a.n_bnd > 0) {
     Scope sc(a.timer, T_BND, st);
-    bnd_update_kernel<R><<<grid_for(a.n_bnd * Rec<R>::NC, 256), 256, 0, st>>>(
-        a.x_in, a.x_out, a.bacc, a.out, a.n_int, a.n_bnd, a.tau);
+    bnd_update_kernel<D><<<grid_for(a.n_bnd, 256), 256, 0, st>>>(a.x_in, a.x_out, a.bacc, a.out,
+                                                                 a.n_rec, a.n_int, a.n_bnd, a.tau);
   }
   return cudaGetLastError();
 }
 
-template <int D, int R>
+template <int D>
 cudaError_t flux_adj_t(const FluxArgs& a, float* lam, float* gw, cudaStream_t st) {
-  const size_t smem = (size_t)a.max_nv * R * sizeof(float) * 3;
-  cudaError_t e = allow_smem(flux_adj_kernel<D, R>, smem);
+  const size_t smem = flux_smem_bytes(a, D, 2);
+  cudaError_t e = allow_smem(flux_adj_kernel<D>, smem);
   if (e != cudaSuccess) return e;
   if (a.k > 0) {
     Scope sc(a.timer, T_EDGE_ADJ, st);
-    flux_adj_kernel<D, R><<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.flist, a.loc, a.w, a.x_in,
-                                                             lam, gw, a.bacc, (int32_t)a.n_int, a.tau);
+    flux_adj_kernel<D><<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w, a.x_in,
+                                                          lam, gw, a.bacc, a.n_rec, a.n_int, a.n_bnd,
+                                                          a.tau);
   }
   if (a.n_bnd > 0) {
     Scope sc(a.timer, T_BND, st);
-    bnd_update_kernel<R><<<grid_for(a.n_bnd * Rec<R>::NC, 256), 256, 0, st>>>(
-        lam, lam, a.bacc, nullptr, a.n_int, a.n_bnd, a.tau);
+    bnd_update_kernel<D><<<grid_for(a.n_bnd, 256), 256, 0, st>>>(lam, lam, a.bacc, nullptr, a.n_rec,
+                                                                 a.n_int, a.n_bnd, a.tau);
   }
   return cudaGetLastError();
 }
@@ -431,28 +513,54 @@ cudaError_t flux_adj_t(const FluxArgs& a, float* lam, float* gw, cudaStream_t st
 
 cudaError_t flux_step(const FluxArgs& a, int D, cudaStream_t st) {
   switch (D) {
-    case 1: return flux_step_t<1, 1>(a, st);
-    case 2: return flux_step_t<2, 2>(a, st);
-    case 3: return flux_step_t<3, 4>(a, st);
-    case 4: return flux_step_t<4, 4>(a, st);
-    case 5: return flux_step_t<5, 8>(a, st);
-    case 6: return flux_step_t<6, 8>(a, st);
-    case 7: return flux_step_t<7, 8>(a, st);
-    case 8: return flux_step_t<8, 8>(a, st);
+    case 1: return flux_step_t<1>(a, st);
+    case 2: return flux_step_t<2>(a, st);
+    case 3: return flux_step_t<3>(a, st);
+    case 4: return flux_step_t<4>(a, st);
+    case 5: return flux_step_t<5>(a, st);
+    case 6: return flux_step_t<6>(a, st);
+    case 7: return flux_step_t<7>(a, st);
+    case 8: return flux_step_t<8>(a, st);
   }
   return cudaErrorInvalidValue;
 }
 
+#define EP_DISPATCH_D(D, CALL) \
+  switch (D) {                    \
+    case 1: CALL(1); break;       \
+    case 2: CALL(2); break;       \
+    case 3: CALL(3); break;       \
+    case 4: CALL(4); break;       \
+    case 5: CALL(5); break;       \
+    case 6: CALL(6); break;       \
+    case 7: CALL(7); break;       \
+    case 8: CALL(8); break;       \
+    default: return cudaErrorInvalidValue; \
+  }
+
+// shared-vertex fold after a pipelined edge kernel: x_out = x_in + tau*bacc
+cudaError_t bnd_update(const FluxArgs& a, int D, float* x_out, const float* x_in, float* out,
+                       cudaStream_t st) {
+  if (a.n_bnd <= 0) return cudaSuccess;
+  Scope sc(a.timer, T_BND, st);
+  const int g = grid_for(a.n_bnd, 256);
+#define EP_BU(DD) \
+  bnd_update_kernel<DD><<<g, 256, 0, st>>>(x_in, x_out, a.bacc, out, a.n_rec, a.n_int, a.n_bnd, a.tau)
+  EP_DISPATCH_D(D, EP_BU)
+#undef EP_BU
+  return cudaGetLastError();
+}
+
 cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st) {
   switch (D) {
-    case 1: return flux_adj_t<1, 1>(a, lam, gw, st);
-    case 2: return flux_adj_t<2, 2>(a, lam, gw, st);
-    case 3: return flux_adj_t<3, 4>(a, lam, gw, st);
-    case 4: return flux_adj_t<4, 4>(a, lam, gw, st);
-    case 5: return flux_adj_t<5, 8>(a, lam, gw, st);
-    case 6: return flux_adj_t<6, 8>(a, lam, gw, st);
-    case 7: return flux_adj_t<7, 8>(a, lam, gw, st);
-    case 8: return flux_adj_t<8, 8>(a, lam, gw, st);
+    case 1: return flux_adj_t<1>(a, lam, gw, st);
+    case 2: return flux_adj_t<2>(a, lam, gw, st);
+    case 3: return flux_adj_t<3>(a, lam, gw, st);
+    case 4: return flux_adj_t<4>(a, lam, gw, st);
+    case 5: return flux_adj_t<5>(a, lam, gw, st);
+    case 6: return flux_adj_t<6>(a, lam, gw, st);
+    case 7: return flux_adj_t<7>(a, lam, gw, st);
+    case 8: return flux_adj_t<8>(a, lam, gw, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -472,31 +580,23 @@ cudaError_t spmv(const SpmvArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t layout_in(const int32_t* rec_of, int64_t n, int D, int R, const float* x, float* x_lay,
-                      cudaStream_t st, Timer* t) {
+cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x,
+                      float* x_lay, cudaStream_t st, Timer* t) {
   Scope sc(t, T_LAYOUT, st);
   const int g = grid_for(n, 256);
-  switch (R) {
-    case 1: layout_in_kernel<1><<<g, 256, 0, st>>>(rec_of, n, D, x, x_lay); break;
-    case 2: layout_in_kernel<2><<<g, 256, 0, st>>>(rec_of, n, D, x, x_lay); break;
-    case 4: layout_in_kernel<4><<<g, 256, 0, st>>>(rec_of, n, D, x, x_lay); break;
-    case 8: layout_in_kernel<8><<<g, 256, 0, st>>>(rec_of, n, D, x, x_lay); break;
-    default: return cudaErrorInvalidValue;
-  }
+#define EP_LIN(DD) layout_in_kernel<DD><<<g, 256, 0, st>>>(rec_of, n, n_rec, x, x_lay)
+  EP_DISPATCH_D(D, EP_LIN)
+#undef EP_LIN
   return cudaGetLastError();
 }
 
-cudaError_t layout_out(const int32_t* rec_of, int64_t n, int D, int R, const float* x_lay, float* x,
-                       cudaStream_t st, Timer* t) {
+cudaError_t layout_out(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x_lay,
+                       float* x, cudaStream_t st, Timer* t) {
   Scope sc(t, T_LAYOUT, st);
   const int g = grid_for(n, 256);
-  switch (R) {
-    case 1: layout_out_kernel<1><<<g, 256, 0, st>>>(rec_of, n, D, x_lay, x); break;
-    case 2: layout_out_kernel<2><<<g, 256, 0, st>>>(rec_of, n, D, x_lay, x); break;
-    case 4: layout_out_kernel<4><<<g, 256, 0, st>>>(rec_of, n, D, x_lay, x); break;
-    case 8: layout_out_kernel<8><<<g, 256, 0, st>>>(rec_of, n, D, x_lay, x); break;
-    default: return cudaErrorInvalidValue;
-  }
+#define EP_LOUT(DD) layout_out_kernel<DD><<<g, 256, 0, st>>>(rec_of, n, n_rec, x_lay, x)
+  EP_DISPATCH_D(D, EP_LOUT)
+#undef EP_LOUT
   return cudaGetLastError();
 }
 

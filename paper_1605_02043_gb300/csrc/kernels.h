@@ -22,15 +22,16 @@ struct FluxArgs {
   const FluxDesc* desc;
   int64_t k;
   const int32_t* flist;
-  const uint32_t* loc;
+  const uint32_t* inc;
+  const uint16_t* ptr;
   const float* w;      // task weights in schedule order
-  const float* x_in;   // state in schedule layout (R floats per record)
+  const float* x_in;   // state in schedule layout (planar, n_rec records)
   float* x_out;        // may equal x_in
-  float* bacc;         // n_bnd * R floats, zero on entry, zero on exit
+  float* bacc;         // n_bnd records (planar), zero on entry, zero on exit
   float* out;          // flux in schedule layout or nullptr
-  int64_t n_int, n_bnd;
+  int64_t n_rec, n_int, n_bnd;
   float tau;
-  int32_t max_nv;
+  int32_t max_np, max_ne, max_nent;
   int tpb;
   Timer* timer;
 };
@@ -62,13 +63,37 @@ struct CostArgs {
   Timer* timer;
 };
 
+// Persistent pipelined kernels (flux_tma.cu): per-stage shared-memory layout
+// (byte offsets, all multiples of 16) and launch plan.
+constexpr int kMaxStages = 4;
+struct TmaLayout {
+  int npos;  // positions per state plane (multiple of 4)
+  int off_lam, off_w, off_ent, off_ptr, off_flist, off_desc;
+  int stage_bytes;
+  int stages;
+  int ahead;  // schedule blocks of look-ahead for L2 prefetch (0: none)
+};
+struct TmaPlan {
+  TmaLayout L;
+  int grid, threads;
+  size_t smem;
+  int* err;  // error word (bit 0: a "full" wait expired, bit 1: an "empty" wait expired)
+};
+cudaError_t flux_fwd_tma(const FluxArgs& a, const TmaPlan& P, int D, cudaStream_t st);
+cudaError_t flux_adj_tma(const FluxArgs& a, const TmaPlan& P, int D, float* lam, float* gw,
+                         cudaStream_t st);
+const void* flux_tma_kernel_ptr(int D, bool adjoint);
+
 cudaError_t flux_step(const FluxArgs& a, int D, cudaStream_t st);
+cudaError_t bnd_update(const FluxArgs& a, int D, float* x_in_out, const float* x_in, float* out,
+                       cudaStream_t st);
 cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st);
 cudaError_t spmv(const SpmvArgs& a, cudaStream_t st);
-cudaError_t layout_in(const int32_t* rec_of, int64_t n, int D, int R, const float* x, float* x_lay,
-                      cudaStream_t st, Timer* t);
-cudaError_t layout_out(const int32_t* rec_of, int64_t n, int D, int R, const float* x_lay, float* x,
-                       cudaStream_t st, Timer* t);
+// n data vertices; state planes of n_rec records
+cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x,
+                      float* x_lay, cudaStream_t st, Timer* t);
+cudaError_t layout_out(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x_lay,
+                       float* x, cudaStream_t st, Timer* t);
 cudaError_t gather(const int32_t* perm, int64_t m, const float* w, float* w_lay, cudaStream_t st,
                    Timer* t);
 cudaError_t scatter_add(const int32_t* perm, int64_t m, const float* w_lay, float* w, cudaStream_t st,

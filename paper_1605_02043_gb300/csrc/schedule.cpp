@@ -11,6 +11,7 @@
 //                    (updated in place by that block) and shared vertices
 //                    (accumulated by atomics), plus 16-bit local slots per task.
 #include <algorithm>
+#include <climits>
 #include <thread>
 
 #include "internal.h"
@@ -89,64 +90,135 @@ void usage(const HostSchedule& s, std::vector<int32_t>& p, std::vector<int32_t>&
     }
 }
 
+// In-block degree of every vertex of block b (tasks of b touching it).
+void block_degrees(const HostSchedule& s, int64_t b, std::vector<int32_t>& deg) {
+  for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
+    int32_t u, v;
+    task_ends(s, s.edge_perm[i], u, v);
+    ++deg[u];
+    if (v != u) ++deg[v];
+  }
+}
+
+// The vertices of V_b satisfying `pick`, first-touch order, then stably
+// sorted by descending in-block degree (so warps see similar list lengths).
+template <typename Pick>
+void class_order(const HostSchedule& s, int64_t b, const std::vector<int32_t>& deg, Pick pick,
+                 std::vector<int32_t>& out) {
+  out.clear();
+  for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i)
+    if (pick(s.vert_list[i])) out.push_back(s.vert_list[i]);
+  std::stable_sort(out.begin(), out.end(), [&](int32_t a, int32_t c) { return deg[a] > deg[c]; });
+}
+
 std::string flux_layout(HostSchedule& s) {
   std::vector<int32_t> p, owner;
   usage(s, p, owner);
   s.rec_of.assign(s.nd, -1);
   s.fdesc.assign(s.k, FluxDesc{});
+  std::vector<int32_t> deg(s.nd, 0), cls;
   int32_t next = 0;
   for (int64_t b = 0; b < s.k; ++b) {
+    block_degrees(s, b, deg);
     s.fdesc[b].int_lo = next;
-    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
-      const int32_t v = s.vert_list[i];
-      if (owner[v] == b && p[v] == 1) s.rec_of[v] = next++;
-    }
+    class_order(s, b, deg, [&](int32_t v) { return owner[v] == b && p[v] == 1; }, cls);
+    for (int32_t v : cls) s.rec_of[v] = next++;
     s.fdesc[b].n_int = next - s.fdesc[b].int_lo;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
   }
   s.n_int = next;
   for (int64_t b = 0; b < s.k; ++b) {
+    block_degrees(s, b, deg);
     s.fdesc[b].bnd_lo = next;
-    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
-      const int32_t v = s.vert_list[i];
-      if (owner[v] == b && p[v] > 1) s.rec_of[v] = next++;
-    }
+    class_order(s, b, deg, [&](int32_t v) { return owner[v] == b && p[v] > 1; }, cls);
+    for (int32_t v : cls) s.rec_of[v] = next++;
     s.fdesc[b].n_ob = next - s.fdesc[b].bnd_lo;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
   }
   s.n_bnd = next - s.n_int;
   for (int64_t v = 0; v < s.nd; ++v)
     if (s.rec_of[v] < 0) s.rec_of[v] = next++;
-  // foreign lists, local slots and packed task slots
+  s.n_rec = (s.nd + 3) / 4 * 4;  // keeps every plane of a state buffer 16-byte aligned
+  // shared-memory positions, foreign lists and per-position incidence lists
   s.flist.clear();
-  s.loc.assign(s.m, 0);
+  s.inc.clear();
+  s.ptr.clear();
+  s.loc.clear();
   s.max_nv = 0;
-  std::vector<int32_t> slot(s.nd, -1);
+  s.max_nent = 0;
+  s.max_nf = 0;
+  s.wmap.clear();
+  auto pad_to = [](auto& v, size_t mult) {
+    while (v.size() % mult) v.push_back(0);
+  };
+  std::vector<int32_t> pos(s.nd, -1);
+  std::vector<int32_t> cnt;
+  std::vector<uint32_t> ent;
   for (int64_t b = 0; b < s.k; ++b) {
     FluxDesc& d = s.fdesc[b];
-    d.e0 = (int32_t)s.block_ptr[b];
     d.ne = (int32_t)(s.block_ptr[b + 1] - s.block_ptr[b]);
+    while (s.wmap.size() % 4) s.wmap.push_back(-1);
+    d.w0 = (int32_t)s.wmap.size();
+    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) s.wmap.push_back(s.edge_perm[i]);
+    pad_to(s.flist, 4);
     d.f0 = (int32_t)s.flist.size();
-    const int32_t own = d.n_int + d.n_ob;
+    d.pi = d.int_lo & 3;
+    d.pb = d.pi + d.n_int;
+    d.pb += ((d.bnd_lo - d.pb) % 4 + 4) % 4;  // pb = bnd_lo (mod 4)
+    d.pf = d.pb + d.n_ob;
     int32_t nf = 0;
+    block_degrees(s, b, deg);
     for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
       const int32_t v = s.vert_list[i];
       const int32_t r = s.rec_of[v];
-      if (owner[v] == b)
-        slot[v] = r < s.n_int ? r - d.int_lo : d.n_int + (r - d.bnd_lo);
-      else {
-        slot[v] = own + nf++;
-        s.flist.push_back(r);
-      }
+      if (owner[v] == b) pos[v] = r < s.n_int ? d.pi + (r - d.int_lo) : d.pb + (r - d.bnd_lo);
     }
+    class_order(s, b, deg, [&](int32_t v) { return owner[v] != b; }, cls);
+    for (int32_t v : cls) {
+      pos[v] = d.pf + nf++;
+      s.flist.push_back(s.rec_of[v]);
+    }
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
     d.nf = nf;
-    const int32_t nv = own + nf;
-    if (nv > 65535) return "block touches more than 65535 vertices";
-    s.max_nv = std::max(s.max_nv, nv);
+    s.max_nf = std::max(s.max_nf, nf);
+    d.np = d.pf + nf;
+    if (d.np > (int32_t)kPosMask + 1) return "block touches too many vertices";
+    s.max_nv = std::max(s.max_nv, d.np);
+    // incidence: every task appears at both endpoints (once for a self loop),
+    // in task order within a position
+    cnt.assign(d.np + 1, 0);
     for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
       int32_t u, v;
       task_ends(s, s.edge_perm[i], u, v);
-      s.loc[i] = (uint32_t)slot[u] | ((uint32_t)slot[v] << 16);
+      ++cnt[pos[u] + 1];
+      if (v != u) ++cnt[pos[v] + 1];
     }
+    for (int32_t p = 0; p < d.np; ++p) cnt[p + 1] += cnt[p];
+    d.nent = cnt[d.np];
+    pad_to(s.inc, 4);
+    pad_to(s.ptr, 8);
+    d.i0 = (int32_t)s.inc.size();
+    d.q0 = (int32_t)s.ptr.size();
+    for (int32_t p = 0; p <= d.np; ++p) s.ptr.push_back((uint16_t)cnt[p]);
+    pad_to(s.ptr, 8);
+    ent.assign(d.nent, 0);
+    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
+      int32_t u, v;
+      task_ends(s, s.edge_perm[i], u, v);
+      const uint32_t j = (uint32_t)(i - s.block_ptr[b]) << kTaskShift;
+      ent[cnt[pos[u]]++] = (uint32_t)pos[v] | j | kSrcBit;
+      if (v != u) ent[cnt[pos[v]]++] = (uint32_t)pos[u] | j;
+    }
+    s.inc.insert(s.inc.end(), ent.begin(), ent.end());
+    pad_to(s.inc, 4);
+    s.max_nent = std::max(s.max_nent, d.nent);
+    if (s.inc.size() >= (size_t)INT32_MAX || s.ptr.size() >= (size_t)INT32_MAX ||
+        s.wmap.size() >= (size_t)INT32_MAX)
+      return "schedule too large";
   }
+  pad_to(s.flist, 4);
+  while (s.wmap.size() % 4) s.wmap.push_back(-1);
+  s.w_pad = (int64_t)s.wmap.size();
   return "";
 }
 
