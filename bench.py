@@ -50,8 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--C", type=int, default=256)
-    ap.add_argument("--threads", type=int, default=128, help="consumer threads per CUDA block")
-    ap.add_argument("--stages", type=int, default=2, help="0: one CUDA block per schedule block")
+    ap.add_argument("--threads", type=int, default=192, help="consumer threads per CUDA block")
+    ap.add_argument("--stages", type=int, default=3, help="0: one CUDA block per schedule block")
     ap.add_argument("--n", type=int, default=1 << 20, help="mesh points (default: the 1M-node mesh)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--sweep", action="store_true", help="also time C in {256, 512, 1024}")

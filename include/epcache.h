@@ -214,13 +214,13 @@ int ep_batch(ep_schedule *const *parts, int32_t count, ep_schedule **out);
 int ep_timing(ep_schedule *s, int32_t enable);
 int ep_timing_read(ep_schedule *s, int32_t kernel_class, double *total_ms, int64_t *launches);
 
-/* Threads per CUDA block of the edge kernels (32..1024, multiple of 32;
- * default 256).  Does not change results beyond FP32 rounding order. */
+/* Threads that compute per CUDA block in the edge kernels (32..1024, multiple
+ * of 32; default 192).  Does not change results beyond FP32 rounding order. */
 int ep_set_threads(ep_schedule *s, int32_t threads);
 
 /*
  * Edge-kernel organisation for flux steps.  stages = 0: one CUDA block per
- * schedule block (stage, compute, write back).  stages = 2..4 (default 2):
+ * schedule block (stage, compute, write back).  stages = 2..4 (default 3):
  * persistent CUDA blocks; a producer warp fills a ring of that many
  * shared-memory stages with 1-D TMA bulk copies of each schedule block's
  * contiguous pieces and pulls the block `ahead` positions later (0..64,

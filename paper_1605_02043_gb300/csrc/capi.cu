@@ -129,7 +129,7 @@ struct EventTimer final : ep::dev::Timer {
 struct ep_schedule {
   ep::HostSchedule h;
   int device = -1;  // device holding the uploaded copy, -1 before upload
-  int tpb = 256;
+  int tpb = 192;
   bool bacc_dirty = true;
   // device copy of the schedule
   DBuf d_desc, d_flist, d_ylist, d_loc, d_inc, d_ptr, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
@@ -139,7 +139,7 @@ struct ep_schedule {
   DBuf ws_hx, ws_hw, ws_hout;
   EventTimer timer;
   ep::dev::Timer* t() { return timer.on ? &timer : nullptr; }
-  int stages = 2;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
+  int stages = 3;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
   int ahead = 4;   // L2 prefetch distance of the pipelined kernels, in schedule blocks per CUDA block
   DBuf ws_ctl;     // [0] block counter, [1] error word
   int sm_count = 0;

@@ -207,44 +207,21 @@ __device__ __forceinline__ StageRefs stage_refs(unsigned char* base, const TmaLa
 __device__ __forceinline__ int pad4(int x) { return (x + 3) & ~3; }
 __device__ __forceinline__ int pad8(int x) { return (x + 7) & ~7; }
 
-// Bulk pieces of one owned run [lo, lo + cnt) at shared positions from p0
-// (p0 = lo mod 4): the 16-byte aligned middle of every plane.  `issue`
-// false only sums the bytes.
+// Bulk pieces of one owned run [lo, lo + cnt) at shared positions from p0:
+// runs start on 4-record boundaries and are followed by unused gap records up
+// to the next boundary, so every plane moves as whole 16-byte chunks
+// (ceil(cnt / (4 / width)) of them).  `issue` false only sums the bytes.
 template <int D, int K = 0>
 __device__ __forceinline__ uint32_t run_bulk(const float* gx, int64_t n, int lo, int cnt, int p0,
                                              float* sx, int npos, uint64_t* bar, bool issue) {
   if constexpr (K < Planes<D>::NP) {
     constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
     constexpr int G = 4 / W;  // records per 16 bytes
-    const int a = (lo + G - 1) / G * G;
-    const int e = (lo + cnt) / G * G;
-    uint32_t bytes = 0;
-    if (e > a) {
-      bytes = (uint32_t)(e - a) * W * 4;
-      if (issue) bulk_load(sx + F * npos + (p0 + (a - lo)) * W, gx + F * n + (int64_t)a * W, bytes, bar);
-    }
+    const uint32_t bytes = (uint32_t)((cnt + G - 1) / G) * 16u;
+    if (issue && bytes) bulk_load(sx + F * npos + p0 * W, gx + F * n + (int64_t)lo * W, bytes, bar);
     return bytes + run_bulk<D, K + 1>(gx, n, lo, cnt, p0, sx, npos, bar, issue);
   }
   return 0;
-}
-// The records of [lo, lo + cnt) that run_bulk leaves out, per plane, copied
-// by lane `lane` of the producer warp with cp.async.
-template <int D, int K = 0>
-__device__ __forceinline__ void run_edges(const float* gx, int64_t n, int lo, int cnt, int p0,
-                                          float* sx, int npos, int lane) {
-  if constexpr (K < Planes<D>::NP) {
-    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
-    constexpr int G = 4 / W;
-    int a = (lo + G - 1) / G * G;
-    int e = (lo + cnt) / G * G;
-    if (e <= a) a = e = lo + cnt;  // no aligned middle: everything is an edge
-    const int nh = a - lo, nt = lo + cnt - e;
-    for (int i = lane; i < nh + nt; i += 32) {
-      const int r = i < nh ? lo + i : e + (i - nh);
-      cp_async<W * 4>(sx + F * npos + (p0 + (r - lo)) * W, gx + F * n + (int64_t)r * W);
-    }
-    run_edges<D, K + 1>(gx, n, lo, cnt, p0, sx, npos, lane);
-  }
 }
 
 // Producer (one thread): bulk copies of schedule block b into stage S.
@@ -327,20 +304,12 @@ __device__ __forceinline__ void prefetch_block(const FluxDesc& d, const int32_t*
   }
 }
 
-// Consumers: cp.async of everything the bulk copies leave out (ragged ends of
-// the owned runs, foreign records), thread `ct` of `nct`.
+// Consumers: cp.async of the foreign records (everything the bulk copies
+// leave out), thread `ct` of `nct`.
 template <int D>
 __device__ __forceinline__ void gather(const StageRefs& S, const TmaLayout& L, const float* x,
                                        const float* lam, int64_t n_rec, int ct, int nct) {
   const FluxDesc& d = *S.desc;
-  if (ct < 32) {
-    run_edges<D>(x, n_rec, d.int_lo, d.n_int, d.pi, S.x, L.npos, ct);
-    run_edges<D>(x, n_rec, d.bnd_lo, d.n_ob, d.pb, S.x, L.npos, ct);
-    if (lam) {
-      run_edges<D>(lam, n_rec, d.int_lo, d.n_int, d.pi, S.lam, L.npos, ct);
-      run_edges<D>(lam, n_rec, d.bnd_lo, d.n_ob, d.pb, S.lam, L.npos, ct);
-    }
-  }
   for (int i = ct; i < d.nf; i += nct) {
     const int32_t r = S.flist[i];
     rec_cp_async<D>(S.x, L.npos, d.pf + i, x, n_rec, r);
@@ -477,19 +446,39 @@ __global__ void __launch_bounds__(1024) flux_fwd_tma_kernel(
       srec_load<D>(S.x, L.npos, p, xp);
 #pragma unroll
       for (int c = 0; c < D; ++c) acc[c] = 0.f;
-      for (int q = k0; q < k1; ++q) {
+      // two entries per iteration: their loads are independent
+      int q = k0;
+      for (; q + 1 < k1; q += 2) {
+        const uint32_t e0 = S.ent[q], e1 = S.ent[q + 1];
+        float xa[D], xb[D];
+        srec_load<D>(S.x, L.npos, (int)(e0 & kPosMask), xa);
+        srec_load<D>(S.x, L.npos, (int)(e1 & kPosMask), xb);
+        const float wa = S.w[(e0 >> kTaskShift) & 0xffffu], wb = S.w[(e1 >> kTaskShift) & 0xffffu];
+        float qa = 0.f, qb = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          xa[c] -= xp[c];
+          xb[c] -= xp[c];
+          qa = fmaf(xa[c], xa[c], qa);
+          qb = fmaf(xb[c], xb[c], qb);
+        }
+        const float ca = __fdividef(wa, 1.f + qa), cb = __fdividef(wb, 1.f + qb);
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc[c] = fmaf(cb, xb[c], fmaf(ca, xa[c], acc[c]));
+      }
+      if (q < k1) {
         const uint32_t e = S.ent[q];
         float xo[D];
         srec_load<D>(S.x, L.npos, (int)(e & kPosMask), xo);
-        float dd[D], s2 = 0.f;
+        float s2 = 0.f;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-          dd[c] = xo[c] - xp[c];
-          s2 = fmaf(dd[c], dd[c], s2);
+          xo[c] -= xp[c];
+          s2 = fmaf(xo[c], xo[c], s2);
         }
         const float coef = __fdividef(S.w[(e >> kTaskShift) & 0xffffu], 1.f + s2);
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc[c] = fmaf(coef, dd[c], acc[c]);
+        for (int c = 0; c < D; ++c) acc[c] = fmaf(coef, xo[c], acc[c]);
       }
       const int32_t r = pos_rec(d, S.flist, p);
       if (p < d.pi + d.n_int) {

@@ -117,28 +117,35 @@ std::string flux_layout(HostSchedule& s) {
   s.rec_of.assign(s.nd, -1);
   s.fdesc.assign(s.k, FluxDesc{});
   std::vector<int32_t> deg(s.nd, 0), cls;
+  // Every run starts on a multiple of 4 records (gap records stay unused), so
+  // a run is a whole number of 16-byte chunks in every state plane.
+  auto align4 = [](int32_t v) { return (v + 3) & ~3; };
   int32_t next = 0;
   for (int64_t b = 0; b < s.k; ++b) {
     block_degrees(s, b, deg);
+    next = align4(next);
     s.fdesc[b].int_lo = next;
     class_order(s, b, deg, [&](int32_t v) { return owner[v] == b && p[v] == 1; }, cls);
     for (int32_t v : cls) s.rec_of[v] = next++;
     s.fdesc[b].n_int = next - s.fdesc[b].int_lo;
     for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
   }
+  next = align4(next);
   s.n_int = next;
   for (int64_t b = 0; b < s.k; ++b) {
     block_degrees(s, b, deg);
+    next = align4(next);
     s.fdesc[b].bnd_lo = next;
     class_order(s, b, deg, [&](int32_t v) { return owner[v] == b && p[v] > 1; }, cls);
     for (int32_t v : cls) s.rec_of[v] = next++;
     s.fdesc[b].n_ob = next - s.fdesc[b].bnd_lo;
     for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
   }
+  next = align4(next);
   s.n_bnd = next - s.n_int;
   for (int64_t v = 0; v < s.nd; ++v)
     if (s.rec_of[v] < 0) s.rec_of[v] = next++;
-  s.n_rec = (s.nd + 3) / 4 * 4;  // keeps every plane of a state buffer 16-byte aligned
+  s.n_rec = align4(next);  // keeps every plane of a state buffer 16-byte aligned
   // shared-memory positions, foreign lists and per-position incidence lists
   s.flist.clear();
   s.inc.clear();
@@ -162,10 +169,11 @@ std::string flux_layout(HostSchedule& s) {
     for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) s.wmap.push_back(s.edge_perm[i]);
     pad_to(s.flist, 4);
     d.f0 = (int32_t)s.flist.size();
-    d.pi = d.int_lo & 3;
-    d.pb = d.pi + d.n_int;
-    d.pb += ((d.bnd_lo - d.pb) % 4 + 4) % 4;  // pb = bnd_lo (mod 4)
-    d.pf = d.pb + d.n_ob;
+    // runs are 4-aligned: positions [0, n_int), [pb, pb + n_ob), [pf, pf + nf)
+    // with pb and pf rounded up to multiples of 4 (room for whole 16-byte chunks)
+    d.pi = 0;
+    d.pb = (d.n_int + 3) & ~3;
+    d.pf = d.pb + ((d.n_ob + 3) & ~3);
     int32_t nf = 0;
     block_degrees(s, b, deg);
     for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {

@@ -128,7 +128,8 @@ def test_layout_round_trip(small_mesh):
         back = torch.zeros_like(x)
         S.layout_out(lay, back)
         assert torch.equal(back, x)
-        assert lay.numel() == D * ((n + 3) // 4 * 4)  # planar, records padded to 4
+        # planar: D planes of n_rec >= n records, n_rec a multiple of 4
+        assert lay.numel() % (4 * D) == 0 and lay.numel() >= D * n
 
 
 def test_step_api_matches_run(small_mesh):
