@@ -240,6 +240,36 @@ int ep_check_errors(ep_schedule *s, int32_t *code, void *stream);
 
 void ep_schedule_free(ep_schedule *s);
 
+/* ---------------------------------------------------- no-allocation variant
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot let a library allocate device memory: code that runs while a
+ * stream is being captured into a CUDA graph (cudaMalloc is not permitted
+ * there), applications that own all device memory through their own pool,
+ * and loops that cannot afford the device synchronisation an allocation may
+ * cause.  It computes what ep_cost() computes, from caller-owned device
+ * arrays, and allocates nothing:
+ *   block_ptr  device int64[k+1]: tasks of block b are positions
+ *              [block_ptr[b], block_ptr[b+1]) of eu/ev
+ *   eu, ev     device int32[m]: the two data-vertex ids of every task, in
+ *              schedule order (ids in [0, nd); a self loop repeats its id)
+ *   max_ne     largest block_ptr[b+1] - block_ptr[b], 1..EP_MAX_C
+ *   counts     device uint64[2], written: [0] = loads = sum_b |V_b|,
+ *              [1] = number of distinct vertices (vertex cut = [0] - [1])
+ * Its only scratch is a fixed array of EP_NOALLOC_MAX_VERTICES one-byte
+ * flags in the library's device memory, which every GPU that loads this part
+ * of the library keeps until the process exits.  nd above that limit gives
+ * EP_EINVAL.  The first call on a device looks up that array's address
+ * (make the first call before any stream capture).  All calls share the
+ * array, so calls whose kernels overlap on the GPU race with each other;
+ * each call clears the flags it uses before counting.  Enqueued on `stream`,
+ * no synchronisation.  Errors: EP_EINVAL, EP_ENODEV, EP_ECUDA, with a
+ * message from ep_noalloc_last_error().
+ */
+#define EP_NOALLOC_MAX_VERTICES (1 << 24)
+int ep_cost_noalloc(const int64_t *block_ptr, const int32_t *eu, const int32_t *ev, int64_t k,
+                    int64_t nd, int32_t max_ne, unsigned long long *counts, void *stream);
+const char *ep_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,8 @@ SIGNATURES = {
     "ep_set_pipeline": (ctypes.c_int, [P, I32, I32]),
     "ep_check_errors": (ctypes.c_int, [P, P, P]),
     "ep_schedule_free": (None, [P]),
+    "ep_cost_noalloc": (ctypes.c_int, [P, P, P, I64, I64, I32, P, P]),
+    "ep_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 
