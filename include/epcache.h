@@ -162,8 +162,8 @@ int ep_layout_in(ep_schedule *s, int32_t D, const float *x, float *x_lay, void *
 /* x <- x_lay (caller layout float[D][n]). */
 int ep_layout_out(ep_schedule *s, int32_t D, const float *x_lay, float *x, void *stream);
 /* Floats of a task-weight buffer in schedule layout: tasks in edge_perm order,
- * each block's run starting on a 16-byte boundary (flux schedules; zero-filled
- * padding between runs), or exactly m for SpMV schedules. */
+ * each block's run starting on a 16-byte boundary (zero-filled padding
+ * between runs). */
 int64_t ep_weights_floats(const ep_schedule *s);
 /* w_lay <- w permuted into schedule layout (padding slots get 0). */
 int ep_weights_in(ep_schedule *s, const float *w, float *w_lay, void *stream);
@@ -177,6 +177,17 @@ int ep_weights_out_add(ep_schedule *s, const float *w_lay, float *w, void *strea
  */
 int ep_step(ep_schedule *s, int32_t D, const float *x_in, float *x_out, const float *w_lay,
             float *out_lay, float tau, void *stream);
+
+/*
+ * SpMV in schedule layout (bipartite schedules, Section 5.2): y_lay = A x_lay
+ * with x_lay over column records and y_lay over row records (n floats each,
+ * ep_spmv_x_in / ep_spmv_y_out permute), w_lay from ep_weights_in.  Rows
+ * used by one block are stored, rows shared by blocks accumulated with
+ * atomics after zeroing.  Buffers 16-byte aligned.
+ */
+int ep_spmv_x_in(ep_schedule *s, const float *x, float *x_lay, void *stream);
+int ep_spmv_y_out(ep_schedule *s, const float *y_lay, float *y, void *stream);
+int ep_spmv(ep_schedule *s, const float *x_lay, const float *w_lay, float *y_lay, void *stream);
 
 /*
  * One adjoint step in schedule layout: lam (in lam_{t+1}, out lam_t) and

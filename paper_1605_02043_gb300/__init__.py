@@ -224,6 +224,16 @@ class Schedule:
         check(lib().ep_step(self._h, D, _vp(x_in), _vp(x_out), _vp(w_lay), _vp(out_lay), tau,
                             _stream(stream)))
 
+    def spmv_x_in(self, x, x_lay, stream=None):
+        check(lib().ep_spmv_x_in(self._h, _vp(x), _vp(x_lay), _stream(stream)))
+
+    def spmv_y_out(self, y_lay, y, stream=None):
+        check(lib().ep_spmv_y_out(self._h, _vp(y_lay), _vp(y), _stream(stream)))
+
+    def spmv(self, x_lay, w_lay, y_lay, stream=None):
+        """y_lay = A x_lay in schedule layout (bipartite schedules)."""
+        check(lib().ep_spmv(self._h, _vp(x_lay), _vp(w_lay), _vp(y_lay), _stream(stream)))
+
     def adjoint_step(self, D: int, x_lay, w_lay, lam, grad_w_lay, tau: float = 1e-3, stream=None):
         check(lib().ep_adjoint_step(self._h, D, _vp(x_lay), _vp(w_lay), _vp(lam), _vp(grad_w_lay),
                                     tau, _stream(stream)))

@@ -37,6 +37,9 @@ SIGNATURES = {
     "ep_weights_out_add": (ctypes.c_int, [P, P, P, P]),
     "ep_step": (ctypes.c_int, [P, I32, P, P, P, P, F32, P]),
     "ep_adjoint_step": (ctypes.c_int, [P, I32, P, P, P, P, F32, P]),
+    "ep_spmv_x_in": (ctypes.c_int, [P, P, P, P]),
+    "ep_spmv_y_out": (ctypes.c_int, [P, P, P, P]),
+    "ep_spmv": (ctypes.c_int, [P, P, P, P, P]),
     "ep_batch": (ctypes.c_int, [P, I32, ctypes.POINTER(P)]),
     "ep_timing": (ctypes.c_int, [P, I32]),
     "ep_timing_read": (ctypes.c_int, [P, I32, P, P]),

@@ -62,3 +62,68 @@ class FluxSteps(torch.autograd.Function):
 def flux_steps(x0, w, sched: Schedule, steps: int, tau: float = 1e-3, every: int = 5):
     """x_T after `steps` explicit flux steps, differentiable in x0 and w."""
     return FluxSteps.apply(x0, w, sched, steps, tau, every)
+
+
+class FluxRunner:
+    """Forward and backward over `steps` flux steps with preallocated buffers.
+
+    Everything lives in the schedule's layout, so one call of run() only
+    enqueues kernels (and device copies) on the current stream and can be
+    captured in a CUDA graph after one warm-up run: forward steps with a
+    checkpoint every `every` steps, then for every segment in reverse a
+    recompute of its states and the adjoint steps.  load() sets x0, w and the
+    loss cotangent g; results() returns dL/dx0 and dL/dw.
+    """
+
+    def __init__(self, sched: Schedule, D: int, steps: int, tau: float = 1e-3, every: int = 5,
+                 device="cuda"):
+        self.s, self.D, self.steps, self.tau, self.every = sched, D, steps, tau, every
+        nl, nw = sched.layout_floats(D), sched.weights_floats()
+        f32 = dict(device=device, dtype=torch.float32)
+        self.x0l = torch.zeros(nl, **f32)
+        self.gl = torch.zeros(nl, **f32)
+        self.xl = torch.zeros(nl, **f32)
+        self.lam = torch.zeros(nl, **f32)
+        self.wl = torch.zeros(nw, **f32)
+        self.gwl = torch.zeros(nw, **f32)
+        nseg = (steps + every - 1) // every
+        self.ckpt = [torch.zeros(nl, **f32) for _ in range(nseg)]
+        self.hist = [torch.zeros(nl, **f32) for _ in range(max(every - 1, 0))]
+
+    def load(self, x0, w, g):
+        self.s.layout_in(x0.contiguous(), self.x0l)
+        self.s.weights_in(w.contiguous(), self.wl)
+        self.s.layout_in(g.contiguous(), self.gl)
+
+    def forward(self):
+        s, D, tau = self.s, self.D, self.tau
+        self.xl.copy_(self.x0l)
+        for t in range(self.steps):
+            if t % self.every == 0:
+                self.ckpt[t // self.every].copy_(self.xl)
+            s.step(D, self.xl, self.xl, self.wl, None, tau)
+
+    def backward(self):
+        s, D, tau = self.s, self.D, self.tau
+        self.lam.copy_(self.gl)
+        self.gwl.zero_()
+        for seg in range(len(self.ckpt) - 1, -1, -1):
+            T = min(self.every, self.steps - seg * self.every)
+            states = [self.ckpt[seg]] + self.hist[: T - 1]
+            for t in range(T - 1):
+                s.step(D, states[t], states[t + 1], self.wl, None, tau)
+            for t in range(T - 1, -1, -1):
+                s.adjoint_step(D, states[t], self.wl, self.lam, self.gwl, tau)
+
+    def run(self):
+        self.forward()
+        self.backward()
+
+    def results(self, x_like, m: int):
+        xT = torch.empty_like(x_like)
+        self.s.layout_out(self.xl, xT)
+        dx0 = torch.empty_like(x_like)
+        self.s.layout_out(self.lam, dx0)
+        dw = torch.zeros(m, device=x_like.device, dtype=torch.float32)
+        self.s.weights_out_add(self.gwl, dw)
+        return xT, dx0, dw

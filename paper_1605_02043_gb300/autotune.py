@@ -1,0 +1,114 @@
+"""Autotuner for the block capacity C and the edge-kernel organisation.
+
+The paper ties C to the thread-block size and picks it by hand (Section 5,
+Table 3: blocks of 256, 512 and 1024 tasks).  Here C (tasks per schedule
+block) and the kernel organisation (pipeline stages, threads per CUDA block)
+are separate knobs, chosen by measurement: for a seeded sample of the graphs
+every candidate C is partitioned by the library, the sample is merged into
+one schedule, and one forward step plus one adjoint step is timed on the GPU
+with CUDA events for every (stages, threads) candidate.  The fastest
+configuration per task wins.  Results are cached in a JSON file keyed by a
+hash of the sample and the candidate lists, so a rerun skips the search.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import Schedule
+
+DEFAULT_CS = (256, 512, 1024)
+DEFAULT_KERNELS = ((3, 192), (2, 192), (3, 128), (3, 256), (2, 256))
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def partition_many(graphs, C: int, threads: int = 0, workers: int | None = None):
+    """Partition (n, src, dst) graphs concurrently (the library call releases the GIL)."""
+    workers = workers or max(1, os.cpu_count() or 1)
+    per_call = 1 if len(graphs) >= workers else threads
+
+    def one(g):
+        n, s, d = g
+        return Schedule.partition(s, d, n, C, threads=per_call)
+
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(one, graphs))
+
+
+def _key(graphs, Cs, kernels, D):
+    h = hashlib.sha256()
+    for n, s, d in graphs:
+        h.update(np.int64(n).tobytes())
+        h.update(np.ascontiguousarray(s).tobytes())
+        h.update(np.ascontiguousarray(d).tobytes())
+    h.update(repr((tuple(Cs), tuple(kernels), D)).encode())
+    return h.hexdigest()[:24]
+
+
+def tune(graphs, D: int = 5, Cs=DEFAULT_CS, kernels=DEFAULT_KERNELS, sample: int = 32,
+         reps: int = 5, seed: int = 0, cache: str | None = CACHE, tau: float = 1e-3):
+    """Best {C, stages, threads} for flux steps on these graphs (list of (n, src, dst))."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(len(graphs), size=min(sample, len(graphs)), replace=False))
+    sub = [graphs[i] for i in idx]
+    key = _key(sub, Cs, kernels, D)
+    if cache and os.path.exists(cache):
+        try:
+            with open(cache) as fh:
+                hit = json.load(fh).get(key)
+            if hit:
+                return hit
+        except (OSError, ValueError):
+            pass
+    n_tot = sum(g[0] for g in sub)
+    table = []
+    for C in Cs:
+        B = Schedule.batch(partition_many(sub, C))
+        x = torch.randn(D, n_tot, device="cuda")
+        w = torch.rand(B.m, device="cuda") + 0.5
+        xl = torch.empty(B.layout_floats(D), device="cuda")
+        wl = torch.empty(B.weights_floats(), device="cuda")
+        lam = torch.empty_like(xl)
+        gw = torch.zeros_like(wl)
+        B.layout_in(x, xl)
+        B.layout_in(x, lam)
+        B.weights_in(w, wl)
+        for stages, threads in kernels:
+            B.set_pipeline(stages)
+            B.set_threads(threads)
+
+            def step():
+                B.step(D, xl, xl, wl, None, tau)
+                B.adjoint_step(D, xl, wl, lam, gw, tau)
+
+            step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                step()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            table.append(dict(C=C, stages=stages, threads=threads, ms=ms, ns_per_task=1e6 * ms / B.m))
+        B.close()
+    best = min(table, key=lambda r: r["ns_per_task"])
+    out = dict(C=best["C"], stages=best["stages"], threads=best["threads"], table=table,
+               sample=[int(i) for i in idx])
+    if cache:
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        try:
+            with open(cache) as fh:
+                allc = json.load(fh)
+        except (OSError, ValueError):
+            allc = {}
+        allc[key] = out
+        with open(cache, "w") as fh:
+            json.dump(allc, fh)
+    return out

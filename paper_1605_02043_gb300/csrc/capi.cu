@@ -143,6 +143,10 @@ struct ep_schedule {
   int ahead = 4;   // L2 prefetch distance of the pipelined kernels, in schedule blocks per CUDA block
   DBuf ws_ctl;     // [0] block counter, [1] error word
   int sm_count = 0;
+  // launch plans of the pipelined kernels, cached per (D, adjoint) so that
+  // steps inside a stream capture only enqueue work
+  ep::dev::TmaPlan plans[EP_MAX_D + 1][2];
+  int plan_key[EP_MAX_D + 1][2] = {};
 };
 
 namespace {
@@ -184,10 +188,12 @@ int ensure_device(ep_schedule* s) {
   CU(upload(s->d_bptr, h.block_ptr));
   CU(upload(s->d_perm, h.edge_perm));
   if (bipartite(s)) {
-    CU(upload(s->d_loc, h.loc));
     CU(upload(s->d_desc, h.sdesc));
     CU(upload(s->d_flist, h.xlist));
     CU(upload(s->d_ylist, h.ylist));
+    CU(upload(s->d_inc, h.sinc));
+    CU(upload(s->d_ptr, h.sptr));
+    CU(upload(s->d_wmap, h.wmap));
     CU(upload(s->d_xrec, h.xrec_of));
     CU(upload(s->d_yrec, h.yrec_of));
   } else {
@@ -206,10 +212,8 @@ cudaStream_t as_stream(void* p) { return static_cast<cudaStream_t>(p); }
 
 // weight layout: flux schedules use the padded per-block layout (wmap),
 // SpMV schedules the plain schedule order (edge_perm)
-const int32_t* wmap_of(ep_schedule* s) {
-  return bipartite(s) ? s->d_perm.as<int32_t>() : s->d_wmap.as<int32_t>();
-}
-int64_t wlen_of(const ep_schedule* s) { return bipartite(s) ? s->h.m : s->h.w_pad; }
+const int32_t* wmap_of(ep_schedule* s) { return s->d_wmap.as<int32_t>(); }
+int64_t wlen_of(const ep_schedule* s) { return s->h.w_pad; }
 
 ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, float* x_out,
                             float* out, float tau) {
@@ -236,8 +240,21 @@ ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, f
   return a;
 }
 
-// Stage layout and grid of the pipelined kernels for state width D.
+int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P);
+
+// Stage layout and grid of the pipelined kernels for state width D (cached;
+// recomputed when the stage count, look-ahead or thread count changes).
 int tma_plan(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
+  const int key = 1 + s->stages + 8 * s->ahead + 1024 * s->tpb;
+  if (s->plan_key[D][adjoint] != key) {
+    if (int rc = tma_plan_compute(s, D, adjoint, s->plans[D][adjoint])) return rc;
+    s->plan_key[D][adjoint] = key;
+  }
+  P = s->plans[D][adjoint];
+  return EP_OK;
+}
+
+int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
   const ep::HostSchedule& h = s->h;
   auto up = [](int64_t x, int64_t m) { return (x + m - 1) / m * m; };
   ep::dev::TmaLayout& L = P.L;
@@ -260,13 +277,21 @@ int tma_plan(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
   CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   L.stages = std::min(s->stages, ep::dev::kMaxStages);
   L.ahead = s->ahead;
-  while (L.stages > 1 && (int64_t)L.stages * L.stage_bytes > optin) --L.stages;
+  optin -= 1024;  // room for the kernel's static shared memory
+  while (L.stages > 2 && (int64_t)L.stages * L.stage_bytes > optin) --L.stages;
   if ((int64_t)L.stages * L.stage_bytes > optin)
     return fail(EP_EINVAL, "a schedule block needs %d bytes of shared memory (limit %d)", L.stage_bytes, optin);
   P.smem = (size_t)L.stages * L.stage_bytes;
   P.threads = 32 * (L.ahead > 0 ? 2 : 1) + s->tpb;  // producer (+ prefetch) warp, consumer warps
   const void* kern = ep::dev::flux_tma_kernel_ptr(D, adjoint);
-  CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem));
+  // the limit is a per-kernel attribute shared by every schedule: open it to
+  // the device maximum (the launch still asks for P.smem)
+  cudaFuncAttributes fa;
+  CU(cudaFuncGetAttributes(&fa, kern));
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // the barriers are static shared memory
+  if ((int64_t)P.smem > dyn_max)
+    return fail(EP_EINVAL, "pipelined stages need %zu bytes of shared memory (limit %d)", P.smem, dyn_max);
+  CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
   int per_sm = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P.threads, P.smem));
   if (per_sm < 1) return fail(EP_EINVAL, "pipelined kernel does not fit on an SM");
@@ -356,6 +381,30 @@ int check_flux(ep_schedule* s, int32_t D) {
   return EP_OK;
 }
 
+// SpMV kernel on schedule-layout buffers
+int spmv_lay(ep_schedule* s, const float* x_lay, const float* w_lay, float* y_lay, cudaStream_t st) {
+  const ep::HostSchedule& h = s->h;
+  ep::dev::SpmvArgs a;
+  a.desc = s->d_desc.as<ep::SpmvDesc>();
+  a.k = h.k;
+  a.xlist = s->d_flist.as<int32_t>();
+  a.ylist = s->d_ylist.as<int32_t>();
+  a.inc = s->d_inc.as<uint32_t>();
+  a.ptr = s->d_ptr.as<uint16_t>();
+  a.w = w_lay;
+  a.x = x_lay;
+  a.y = y_lay;
+  a.ny_int = h.ny_int;
+  a.ny_zero = h.n - h.ny_int;
+  a.max_nx = h.max_nx;
+  a.max_ny = h.max_ny;
+  a.max_ne = h.max_ne;
+  a.tpb = s->tpb;
+  a.timer = s->t();
+  CU(ep::dev::spmv(a, st));
+  return EP_OK;
+}
+
 int run_spmv(ep_schedule* s, const float* x, const float* w, float* y, cudaStream_t st) {
   const ep::HostSchedule& h = s->h;
   CU(s->ws_x.ensure((size_t)h.n * sizeof(float)));
@@ -363,22 +412,8 @@ int run_spmv(ep_schedule* s, const float* x, const float* w, float* y, cudaStrea
   CU(s->ws_w.ensure((size_t)wlen_of(s) * sizeof(float)));
   CU(ep::dev::layout_in(s->d_xrec.as<int32_t>(), h.n, h.n, 1, x, s->ws_x.as<float>(), st, s->t()));
   CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
-  ep::dev::SpmvArgs a;
-  a.desc = s->d_desc.as<ep::SpmvDesc>();
-  a.k = h.k;
-  a.xlist = s->d_flist.as<int32_t>();
-  a.ylist = s->d_ylist.as<int32_t>();
-  a.loc = s->d_loc.as<uint32_t>();
-  a.w = s->ws_w.as<float>();
-  a.x = s->ws_x.as<float>();
-  a.y = s->ws_out.as<float>();
-  a.ny_int = h.ny_int;
-  a.ny_zero = h.n - h.ny_int;
-  a.max_nx = h.max_nx;
-  a.max_ny = h.max_ny;
-  a.tpb = s->tpb;
-  a.timer = s->t();
-  CU(ep::dev::spmv(a, st));
+  if (int rc = spmv_lay(s, s->ws_x.as<float>(), s->ws_w.as<float>(), s->ws_out.as<float>(), st))
+    return rc;
   CU(ep::dev::layout_out(s->d_yrec.as<int32_t>(), h.n, h.n, 1, s->ws_out.as<float>(), y, st, s->t()));
   return EP_OK;
 }
@@ -748,6 +783,37 @@ int ep_timing_read(ep_schedule* s, int32_t kernel_class, double* total_ms, int64
   if (total_ms) *total_ms = s->timer.total[kernel_class];
   if (launches) *launches = s->timer.count[kernel_class];
   return EP_OK;
+}
+
+int check_spmv(ep_schedule* s) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (!bipartite(s)) return fail(EP_EINVAL, "SpMV needs a bipartite schedule");
+  return ensure_device(s);
+}
+
+int ep_spmv_x_in(ep_schedule* s, const float* x, float* x_lay, void* stream) {
+  g_error.clear();
+  if (int rc = check_spmv(s)) return rc;
+  if (!x || !x_lay) return fail(EP_EINVAL, "null argument");
+  CU(ep::dev::layout_in(s->d_xrec.as<int32_t>(), s->h.n, s->h.n, 1, x, x_lay, as_stream(stream), s->t()));
+  return EP_OK;
+}
+
+int ep_spmv_y_out(ep_schedule* s, const float* y_lay, float* y, void* stream) {
+  g_error.clear();
+  if (int rc = check_spmv(s)) return rc;
+  if (!y || !y_lay) return fail(EP_EINVAL, "null argument");
+  CU(ep::dev::layout_out(s->d_yrec.as<int32_t>(), s->h.n, s->h.n, 1, y_lay, y, as_stream(stream), s->t()));
+  return EP_OK;
+}
+
+int ep_spmv(ep_schedule* s, const float* x_lay, const float* w_lay, float* y_lay, void* stream) {
+  g_error.clear();
+  if (int rc = check_spmv(s)) return rc;
+  if (!x_lay || !w_lay || !y_lay) return fail(EP_EINVAL, "null argument");
+  if (misaligned(x_lay) || misaligned(w_lay) || misaligned(y_lay))
+    return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
+  return spmv_lay(s, x_lay, w_lay, y_lay, as_stream(stream));
 }
 
 int ep_set_pipeline(ep_schedule* s, int32_t stages, int32_t ahead) {

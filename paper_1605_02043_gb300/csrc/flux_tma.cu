@@ -550,9 +550,7 @@ __global__ void __launch_bounds__(1024) flux_adj_tma_kernel(
 
 template <int D>
 cudaError_t launch_fwd(const FluxArgs& a, const TmaPlan& P, cudaStream_t st) {
-  auto kern = flux_fwd_tma_kernel<D>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem);
-  if (e != cudaSuccess) return e;
+  auto kern = flux_fwd_tma_kernel<D>;  // shared-memory limit raised when the plan was made
   kern<<<P.grid, P.threads, P.smem, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w, a.x_in, a.x_out, a.bacc,
                                           a.out, a.n_rec, a.n_int, a.n_bnd, a.tau, a.k, P.err, P.L);
   return cudaGetLastError();
@@ -560,9 +558,7 @@ cudaError_t launch_fwd(const FluxArgs& a, const TmaPlan& P, cudaStream_t st) {
 
 template <int D>
 cudaError_t launch_adj(const FluxArgs& a, const TmaPlan& P, float* lam, float* gw, cudaStream_t st) {
-  auto kern = flux_adj_tma_kernel<D>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P.smem);
-  if (e != cudaSuccess) return e;
+  auto kern = flux_adj_tma_kernel<D>;  // shared-memory limit raised when the plan was made
   kern<<<P.grid, P.threads, P.smem, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w, a.x_in, lam, gw, a.bacc,
                                           a.n_rec, a.n_int, a.n_bnd, a.tau, a.k, P.err, P.L);
   return cudaGetLastError();

@@ -40,14 +40,17 @@ constexpr int kTaskShift = 15;
 constexpr uint32_t kSrcBit = 0x80000000u;
 
 // SpMV kernels (bipartite): x records are read only, y records accumulate.
-//   x slots: [0, n_xo) contiguous from x_lo, then n_xf from xlist[fx0..]
-//   y slots: [0, n_yi) interior from yi_lo, [n_yi, n_yi + n_yob) from yb_lo,
-//            then n_yf from ylist[fy0..]
+// x positions: [0, n_xo) the run x_lo.., then n_xf ids from xlist[fx0..].
+// y positions: [0, n_yi) the single-block rows yi_lo.., [n_yi, n_yi + n_yob)
+// the run yb_lo.. of shared rows first touched here, then n_yf ids from
+// ylist[fy0..]; within each class rows are ordered by descending list length.
+// Row position p has entries ent[i0 + ptr[q0 + p] .. i0 + ptr[q0 + p + 1]):
+// (x position) | (task << 15); task weights are w_lay[w0 .. w0 + ne).
 struct SpmvDesc {
-  int32_t e0, ne;
+  int32_t w0, ne;
   int32_t x_lo, n_xo, fx0, n_xf;
   int32_t yi_lo, n_yi, yb_lo, n_yob, fy0, n_yf;
-  int32_t pad[4];
+  int32_t i0, q0, pad[2];
 };
 static_assert(sizeof(SpmvDesc) == 64, "SpmvDesc layout");
 
@@ -83,6 +86,8 @@ struct HostSchedule {
   std::vector<int32_t> xrec_of, yrec_of;  // by column / row index
   std::vector<SpmvDesc> sdesc;
   std::vector<int32_t> xlist, ylist;
+  std::vector<uint32_t> sinc;   // SpMV row entries
+  std::vector<uint16_t> sptr;   // SpMV row offsets
   int32_t max_nx = 0, max_ny = 0;
 
   std::vector<uint32_t> loc;  // per task in edge_perm order: slot(u) | slot(v) << 16

@@ -11,6 +11,8 @@
 
 #include <climits>
 #include <cstdint>
+#include <mutex>
+#include <unordered_set>
 
 #include "kernels.h"
 
@@ -307,32 +309,62 @@ __global__ void __launch_bounds__(1024) flux_adj_kernel(
 
 // --------------------------------------------------------------------- SpMV
 
-__global__ void spmv_kernel(const SpmvDesc* __restrict__ desc, const int32_t* __restrict__ xlist,
-                            const int32_t* __restrict__ ylist, const uint32_t* __restrict__ loc,
-                            const float* __restrict__ w, const float* __restrict__ x,
-                            float* __restrict__ y) {
+// One CUDA block per schedule block, pull form: x of the block's columns is
+// staged in shared memory; every row position sums w * x over its list.
+// Rows with more than 32 entries (hubs of a power-law matrix) take a whole
+// warp each; the others one thread each.
+__device__ __forceinline__ void spmv_write(const SpmvDesc& d, const int32_t* __restrict__ ylist,
+                                           float* __restrict__ y, int p, float acc) {
+  if (p < d.n_yi) {
+    y[d.yi_lo + p] = acc;
+  } else {
+    const int own = d.n_yi + d.n_yob;
+    const int32_t r = p < own ? d.yb_lo + (p - d.n_yi) : __ldg(ylist + d.fy0 + (p - own));
+    atomicAdd(y + r, acc);
+  }
+}
+
+__global__ void __launch_bounds__(1024) spmv_kernel(
+    const SpmvDesc* __restrict__ desc, const int32_t* __restrict__ xlist,
+    const int32_t* __restrict__ ylist, const uint32_t* __restrict__ inc,
+    const uint16_t* __restrict__ ptr, const float* __restrict__ w, const float* __restrict__ x,
+    float* __restrict__ y) {
   extern __shared__ float4 smem4[];
   const SpmvDesc d = desc[blockIdx.x];
   const int nx = d.n_xo + d.n_xf, ny = d.n_yi + d.n_yob + d.n_yf;
   float* xs = reinterpret_cast<float*>(smem4);
-  float* ys = xs + nx;
+  float* ws = xs + ((nx + 3) & ~3);
+  uint32_t* es = reinterpret_cast<uint32_t*>(ws + ((d.ne + 3) & ~3));
+  uint16_t* ps = reinterpret_cast<uint16_t*>(es + d.ne);
+  for (int i = threadIdx.x; i < d.ne; i += blockDim.x) {
+    ws[i] = __ldg(w + d.w0 + i);
+    es[i] = __ldg(inc + d.i0 + i);
+  }
+  for (int i = threadIdx.x; i <= ny; i += blockDim.x) ps[i] = __ldg(ptr + d.q0 + i);
   for (int i = threadIdx.x; i < nx; i += blockDim.x)
     xs[i] = __ldg(x + (i < d.n_xo ? d.x_lo + i : __ldg(xlist + d.fx0 + (i - d.n_xo))));
-  for (int i = threadIdx.x; i < ny; i += blockDim.x) ys[i] = 0.f;
   __syncthreads();
-  for (int j = threadIdx.x; j < d.ne; j += blockDim.x) {
-    const uint32_t p = __ldg(loc + d.e0 + j);
-    atomicAdd(ys + (p & 0xffffu), __ldg(w + d.e0 + j) * xs[p >> 16]);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < ny; i += blockDim.x) {
-    if (i < d.n_yi) {
-      y[d.yi_lo + i] = ys[i];
-    } else {
-      const int own = d.n_yi + d.n_yob;
-      const int32_t r = i < own ? d.yb_lo + (i - d.n_yi) : __ldg(ylist + d.fy0 + (i - own));
-      atomicAdd(y + r, ys[i]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int p = warp; p < ny; p += nw) {
+    const int k0 = ps[p], k1 = ps[p + 1];
+    if (k1 - k0 <= 32) continue;  // warp-uniform
+    float acc = 0.f;
+    for (int q = k0 + lane; q < k1; q += 32) {
+      const uint32_t e = es[q];
+      acc = fmaf(ws[e >> kTaskShift], xs[e & kPosMask], acc);
     }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) spmv_write(d, ylist, y, p, acc);
+  }
+  for (int p = threadIdx.x; p < ny; p += blockDim.x) {
+    const int k0 = ps[p], k1 = ps[p + 1];
+    if (k1 - k0 > 32 || k1 == k0) continue;
+    float acc = 0.f;
+    for (int q = k0; q < k1; ++q) {
+      const uint32_t e = es[q];
+      acc = fmaf(ws[e >> kTaskShift], xs[e & kPosMask], acc);
+    }
+    spmv_write(d, ylist, y, p, acc);
   }
 }
 
@@ -447,10 +479,29 @@ int grid_for(int64_t work, int tpb) {
   return (int)g;
 }
 
+// Opens a kernel's dynamic shared-memory limit to the device maximum once
+// (a per-kernel attribute shared by all callers); launches above 48 KB need it.
+std::mutex g_smem_mu;
+std::unordered_set<const void*> g_smem_opened;  // kernels whose limit is open
+
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;  // minus the kernel's static shared memory
+  if (bytes > (size_t)dyn_max) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  const void* key = reinterpret_cast<const void*>(kernel);
+  if (g_smem_opened.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+  if (e == cudaSuccess) g_smem_opened.insert(key);
+  return e;
 }
 
 struct Scope {
@@ -566,7 +617,8 @@ cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, c
 }
 
 cudaError_t spmv(const SpmvArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)(a.max_nx + a.max_ny) * sizeof(float);
+  const size_t smem = (size_t)(a.max_nx + 4) * sizeof(float) + (size_t)(a.max_ne + 4) * 8 +
+                      (size_t)(a.max_ny + 1) * sizeof(uint16_t) + 16;
   cudaError_t e = allow_smem(spmv_kernel, smem);
   if (e != cudaSuccess) return e;
   if (a.ny_zero > 0) {
@@ -575,7 +627,7 @@ cudaError_t spmv(const SpmvArgs& a, cudaStream_t st) {
   }
   if (a.k > 0) {
     Scope sc(a.timer, T_SPMV, st);
-    spmv_kernel<<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.xlist, a.ylist, a.loc, a.w, a.x, a.y);
+    spmv_kernel<<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.xlist, a.ylist, a.inc, a.ptr, a.w, a.x, a.y);
   }
   return cudaGetLastError();
 }

@@ -41,12 +41,13 @@ struct SpmvArgs {
   int64_t k;
   const int32_t* xlist;
   const int32_t* ylist;
-  const uint32_t* loc;
-  const float* w;
-  const float* x;   // x records
-  float* y;         // y records; [ny_int, ny_int + ny_zero) zeroed first
+  const uint32_t* inc;   // row entries
+  const uint16_t* ptr;   // row offsets
+  const float* w;        // padded weight layout
+  const float* x;        // x records
+  float* y;              // y records; [ny_int, ny_int + ny_zero) zeroed first
   int64_t ny_int, ny_zero;
-  int32_t max_nx, max_ny;
+  int32_t max_nx, max_ny, max_ne;
   int tpb;
   Timer* timer;
 };

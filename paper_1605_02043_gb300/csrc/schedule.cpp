@@ -237,6 +237,7 @@ std::string spmv_layout(HostSchedule& s) {
   s.xrec_of.assign(n, -1);
   s.yrec_of.assign(n, -1);
   s.sdesc.assign(s.k, SpmvDesc{});
+  std::vector<int32_t> deg(s.nd, 0), cls;
   // x records: cpack order restricted to columns
   int32_t nx = 0;
   for (int64_t b = 0; b < s.k; ++b) {
@@ -250,73 +251,102 @@ std::string spmv_layout(HostSchedule& s) {
   }
   for (int32_t j = 0; j < n; ++j)
     if (s.xrec_of[j] < 0) s.xrec_of[j] = nx++;
-  // y records: single-block rows first, then shared rows
+  // y records: single-block rows first, then shared rows; longest lists first
   int32_t ny = 0;
   for (int64_t b = 0; b < s.k; ++b) {
     SpmvDesc& d = s.sdesc[b];
+    block_degrees(s, b, deg);
     d.yi_lo = ny;
-    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
-      const int32_t v = s.vert_list[i];
-      if (v >= n && owner[v] == b && p[v] == 1) s.yrec_of[v - n] = ny++;
-    }
+    class_order(s, b, deg, [&](int32_t v) { return v >= n && owner[v] == b && p[v] == 1; }, cls);
+    for (int32_t v : cls) s.yrec_of[v - n] = ny++;
     d.n_yi = ny - d.yi_lo;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
   }
   s.ny_int = ny;
   for (int64_t b = 0; b < s.k; ++b) {
     SpmvDesc& d = s.sdesc[b];
+    block_degrees(s, b, deg);
     d.yb_lo = ny;
-    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
-      const int32_t v = s.vert_list[i];
-      if (v >= n && owner[v] == b && p[v] > 1) s.yrec_of[v - n] = ny++;
-    }
+    class_order(s, b, deg, [&](int32_t v) { return v >= n && owner[v] == b && p[v] > 1; }, cls);
+    for (int32_t v : cls) s.yrec_of[v - n] = ny++;
     d.n_yob = ny - d.yb_lo;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
   }
   s.ny_bnd = ny - s.ny_int;
   for (int32_t i = 0; i < n; ++i)
     if (s.yrec_of[i] < 0) s.yrec_of[i] = ny++;
   s.xlist.clear();
   s.ylist.clear();
-  s.loc.assign(s.m, 0);
+  s.sinc.clear();
+  s.sptr.clear();
+  s.wmap.clear();
+  s.loc.clear();
   s.max_nx = s.max_ny = 0;
-  std::vector<int32_t> slot(s.nd, -1);
+  s.max_nent = 0;
+  std::vector<int32_t> pos(s.nd, -1), cnt;
+  std::vector<uint32_t> ent;
   for (int64_t b = 0; b < s.k; ++b) {
     SpmvDesc& d = s.sdesc[b];
-    d.e0 = (int32_t)s.block_ptr[b];
     d.ne = (int32_t)(s.block_ptr[b + 1] - s.block_ptr[b]);
+    while (s.wmap.size() % 4) s.wmap.push_back(-1);
+    d.w0 = (int32_t)s.wmap.size();
+    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) s.wmap.push_back(s.edge_perm[i]);
     d.fx0 = (int32_t)s.xlist.size();
     d.fy0 = (int32_t)s.ylist.size();
-    int32_t nxf = 0, nyf = 0;
+    int32_t nxf = 0;
     for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
       const int32_t v = s.vert_list[i];
-      if (v < n) {
-        if (owner[v] == b)
-          slot[v] = s.xrec_of[v] - d.x_lo;
-        else {
-          slot[v] = d.n_xo + nxf++;
-          s.xlist.push_back(s.xrec_of[v]);
-        }
-      } else {
-        const int32_t r = s.yrec_of[v - n];
-        if (owner[v] == b)
-          slot[v] = r < s.ny_int ? r - d.yi_lo : d.n_yi + (r - d.yb_lo);
-        else {
-          slot[v] = d.n_yi + d.n_yob + nyf++;
-          s.ylist.push_back(r);
-        }
+      if (v >= n) continue;
+      if (owner[v] == b)
+        pos[v] = s.xrec_of[v] - d.x_lo;
+      else {
+        pos[v] = d.n_xo + nxf++;
+        s.xlist.push_back(s.xrec_of[v]);
       }
     }
     d.n_xf = nxf;
+    block_degrees(s, b, deg);
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      if (v < n || owner[v] != b) continue;
+      const int32_t r = s.yrec_of[v - n];
+      pos[v] = r < s.ny_int ? r - d.yi_lo : d.n_yi + (r - d.yb_lo);
+    }
+    class_order(s, b, deg, [&](int32_t v) { return v >= n && owner[v] != b; }, cls);
+    int32_t nyf = 0;
+    for (int32_t v : cls) {
+      pos[v] = d.n_yi + d.n_yob + nyf++;
+      s.ylist.push_back(s.yrec_of[v - n]);
+    }
     d.n_yf = nyf;
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
     const int32_t nxs = d.n_xo + nxf, nys = d.n_yi + d.n_yob + nyf;
-    if (nxs > 65535 || nys > 65535) return "block touches more than 65535 vertices";
+    if (nxs > (int32_t)kPosMask + 1 || nys > 65535) return "block touches too many vertices";
     s.max_nx = std::max(s.max_nx, nxs);
     s.max_ny = std::max(s.max_ny, nys);
+    // row lists: (x position) | (task << 15), tasks in schedule order
+    cnt.assign(nys + 1, 0);
     for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
       int32_t u, v;
       task_ends(s, s.edge_perm[i], u, v);
-      s.loc[i] = (uint32_t)slot[u] | ((uint32_t)slot[v] << 16);  // (y slot, x slot)
+      ++cnt[pos[u] + 1];
     }
+    for (int32_t q = 0; q < nys; ++q) cnt[q + 1] += cnt[q];
+    d.i0 = (int32_t)s.sinc.size();
+    d.q0 = (int32_t)s.sptr.size();
+    for (int32_t q = 0; q <= nys; ++q) s.sptr.push_back((uint16_t)cnt[q]);
+    ent.assign(d.ne, 0);
+    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
+      int32_t u, v;
+      task_ends(s, s.edge_perm[i], u, v);
+      ent[cnt[pos[u]]++] = (uint32_t)pos[v] | ((uint32_t)(i - s.block_ptr[b]) << kTaskShift);
+    }
+    s.sinc.insert(s.sinc.end(), ent.begin(), ent.end());
+    s.max_nent = std::max(s.max_nent, d.ne);
+    if (s.sinc.size() >= (size_t)INT32_MAX) return "schedule too large";
   }
+  while (s.wmap.size() % 4) s.wmap.push_back(-1);
+  s.w_pad = (int64_t)s.wmap.size();
   return "";
 }
 

@@ -154,13 +154,15 @@ def test_step_api_matches_run(small_mesh):
     assert rel_l2(out.cpu().numpy(), fT) <= RTOL
 
 
-@pytest.mark.parametrize("C,default_order", [(512, False), (512, True), (64, False)])
-def test_spmv_rmat(C, default_order):
+@pytest.mark.parametrize("C,default_order,threads", [(512, False, 192), (512, True, 192), (64, False, 64),
+                                                     (2048, True, 256), (1000, False, 1024)])
+def test_spmv_rmat(C, default_order, threads):
     scale = 12
     n = 1 << scale
     r, c = W.rmat(scale=scale, m_draws=1 << 16, seed=1)
     x0, w = W.spmv_inputs(n, r.size, 0)
     S = E.Schedule.partition(r, c, n, C, bipartite=True, default_order=default_order)
+    S.set_threads(threads)
     check_schedule_matches_oracle(S, O.ep_schedule(r, c, n, C, bipartite=True,
                                                    default_order=default_order))
     y = torch.full((n,), 3.0, device="cuda")
@@ -170,6 +172,16 @@ def test_spmv_rmat(C, default_order):
     # rows without tasks are zero
     empty = np.setdiff1d(np.arange(n), r)
     assert torch.all(y[torch.from_numpy(empty).cuda()] == 0)
+    # schedule-layout entry points give the same y
+    xl = torch.empty(n, device="cuda")
+    wl = torch.empty(S.weights_floats(), device="cuda")
+    yl = torch.full((n,), 5.0, device="cuda")
+    S.spmv_x_in(cuda(x0), xl)
+    S.weights_in(cuda(w), wl)
+    S.spmv(xl, wl, yl)
+    y2 = torch.empty(n, device="cuda")
+    S.spmv_y_out(yl, y2)
+    assert rel_l2(y2.cpu().numpy(), ref) <= RTOL
 
 
 @pytest.mark.parametrize("stages", [0, 3])
@@ -241,3 +253,59 @@ def test_errors_are_reported(small_mesh):
         S.step(5, xl[1:], xl[1:], wl)  # schedule-layout buffers must be 16-byte aligned
     with pytest.raises(E.EpError):
         S.set_pipeline(1)
+
+
+def test_autograd_function_matches_oracle(small_mesh):
+    from paper_1605_02043_gb300.autograd import flux_steps
+
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 256)
+    x0 = W.flux_state(n, 5, 0)
+    w = W.flux_weights(src.size, 0)
+    g = W.loss_weights(n, 5, 1)
+    T, tau = 10, 1e-3
+    xT_ref, _ = O.flux_steps(src, dst, x0, w, T, tau)
+    dx_ref, dw_ref = O.flux_adjoint(src, dst, x0, w, T, tau, g)
+    for every in (5, 3, 10):
+        x = cuda(x0).requires_grad_(True)
+        wt = cuda(w).requires_grad_(True)
+        xT = flux_steps(x, wt, S, T, tau, every)
+        xT.backward(cuda(g))
+        assert rel_l2(xT.detach().cpu().numpy(), xT_ref) <= RTOL
+        assert rel_l2(x.grad.cpu().numpy(), dx_ref) <= RTOL, every
+        assert rel_l2(wt.grad.cpu().numpy(), dw_ref) <= RTOL, every
+
+
+def test_runner_in_cuda_graph_matches_eager_and_oracle():
+    from paper_1605_02043_gb300.autograd import FluxRunner
+
+    meshes = [W.knn_mesh(nn, 4, 60 + i) for i, nn in enumerate((900, 1300, 2100, 3000))]
+    sizes = (900, 1300, 2100, 3000)
+    parts = [E.Schedule.partition(s, d, nn, 128) for (s, d), nn in zip(meshes, sizes)]
+    B = E.Schedule.batch(parts)
+    offs = np.cumsum((0,) + sizes[:-1])
+    src = np.concatenate([s + o for (s, _), o in zip(meshes, offs)]).astype(np.int32)
+    dst = np.concatenate([d + o for (_, d), o in zip(meshes, offs)]).astype(np.int32)
+    n = sum(sizes)
+    x0 = W.flux_state(n, 5, 9)
+    w = W.flux_weights(src.size, 9)
+    g = W.loss_weights(n, 5, 2)
+    T, tau = 12, 1e-3
+    R = FluxRunner(B, 5, T, tau, every=5)
+    R.load(cuda(x0), cuda(w), cuda(g))
+    R.run()  # warm-up: allocates the library workspace outside the capture
+    torch.cuda.synchronize()
+    xT_e, dx_e, dw_e = R.results(cuda(x0), B.m)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        R.run()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    xT_g, dx_g, dw_g = R.results(cuda(x0), B.m)
+    assert rel_l2(xT_g.cpu().numpy(), xT_e.cpu().numpy()) <= RTOL
+    assert rel_l2(dx_g.cpu().numpy(), dx_e.cpu().numpy()) <= RTOL
+    dx_ref, dw_ref = O.flux_adjoint(src, dst, x0, w, T, tau, g)
+    assert rel_l2(dx_g.cpu().numpy(), dx_ref) <= RTOL
+    assert rel_l2(dw_g.cpu().numpy(), dw_ref) <= RTOL
+    assert B.check_errors() == 0
