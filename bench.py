@@ -556,9 +556,12 @@ def main():
             tr = json.load(open(tr_path))
             from paper_1605_02043_gb300 import build as B
             import hashlib
-            h = hashlib.sha256(open(os.path.join(B.CSRC, "kernels.cu"), "rb").read()).hexdigest()[:16]
+            hh = hashlib.sha256()
+            for f in ("kernels.cu", "flux_tma.cu"):
+                hh.update(open(os.path.join(B.CSRC, f), "rb").read())
+            h = hh.hexdigest()[:16]
             ent = tr.get(f"flux_fwd_C{args.C}_n{n}")
-            if ent and ent.get("kernels_cu_sha") == h:
+            if ent and ent.get("kernel_sources_sha") == h:
                 traffic = ent["dram_bytes_per_launch"]
         except Exception:
             traffic = None
