@@ -29,6 +29,9 @@
  *              id) whose combined vertex weight is <= maxw = max(1, min(sL,
  *              W-sL)/16); coarse ids in order of the smaller member; stop (and
  *              drop the level) when it shrinks the graph by less than 10%;
+ *              stop after a level whose adjacency (entries, both directions)
+ *              shrank by less than 15% (dense coarse graphs of power-law
+ *              inputs);
  *     initial  graph growing: start at the last vertex dequeued by a BFS from
  *              vertex 0 (neighbours ascending); BFS from there adding each
  *              dequeued vertex to the left while it fits (a vertex that does
@@ -475,6 +478,8 @@ static void bisect(const graph_t *g0, int64_t sL, uint8_t *side0) {
     free(mate);
     cmaps[L] = cmap;
     lev[++L] = cg;
+    /* a level whose adjacency shrank by less than 15% ends the coarsening */
+    if (cg.xadj[cg.n] * 20 > g->xadj[g->n] * 17) break;
   }
   uint8_t *side = malloc((size_t)lev[L].n);
   grow_bisection(&lev[L], sL, side);

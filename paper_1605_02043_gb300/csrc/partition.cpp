@@ -9,7 +9,8 @@
 // instead, so the schedule does not depend on thread count or timing:
 //   coarsening   heavy-edge matching in ascending vertex order, ties to the
 //                smaller neighbour, combined weight <= max(1, min(sL,W-sL)/16),
-//                while n > 64 and each level shrinks by >= 10%;
+//                while n > 64 and each level shrinks by >= 10%; a level whose
+//                adjacency shrank by < 15% is kept but ends the coarsening;
 //   initial cut  graph growing from the last vertex of a BFS from vertex 0;
 //   refinement   4 passes of positive-gain moves in (gain desc, id asc) order
 //                under the balance window max(tol, |lw - sL|),
@@ -21,8 +22,6 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
-#include <map>
-#include <set>
 #include <thread>
 
 namespace ep {
@@ -30,6 +29,25 @@ namespace {
 
 constexpr int32_t kCoarsenMin = 64;
 constexpr int kPasses = 4;
+constexpr int32_t kParallelMin = 1 << 20;  // graphs this large split loops over host threads
+
+// fn(lo, hi, t) over [0, n) in `parts` contiguous ranges (part t = [lo, hi)).
+template <typename Fn>
+void for_ranges(int64_t n, int parts, Fn fn) {
+  if (parts <= 1) {
+    fn((int64_t)0, n, 0);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < parts; ++t)
+    pool.emplace_back([&, t]() { fn(n * t / parts, n * (t + 1) / parts, t); });
+  for (auto& th : pool) th.join();
+}
+
+int loop_parts(int64_t n) {
+  if (n < kParallelMin) return 1;
+  return (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+}
 
 struct Graph {
   int32_t n = 0;
@@ -138,44 +156,58 @@ int32_t heavy_edge_matching(const Graph& g, int32_t maxw, std::vector<int32_t>& 
   return (int32_t)lead.size();
 }
 
+// Coarse graph: the row of a coarse vertex is the union of its members' rows
+// mapped to coarse ids, without the coarse vertex itself, parallel entries
+// merged by summing weights, ascending.  Rows are built independently
+// (ranges of coarse vertices on host threads for large graphs) and joined.
 void contract(const Graph& g, const std::vector<int32_t>& cmap, const std::vector<int32_t>& lead,
               const std::vector<int32_t>& other, Graph& cg) {
   const int32_t nc = (int32_t)lead.size();
   cg.n = nc;
   cg.xadj.assign(nc + 1, 0);
   cg.vw.assign(nc, 0);
-  cg.adj.clear();
-  cg.ew.clear();
-  cg.adj.reserve(g.adj.size());
-  cg.ew.reserve(g.adj.size());
-  std::vector<int32_t> slot(nc, -1);  // position of a coarse neighbour in the row
-  std::vector<std::pair<int32_t, int32_t>> row;
-  for (int32_t c = 0; c < nc; ++c) {
-    row.clear();
-    const int32_t mem[2] = {lead[c], other[c]};
-    for (int i = 0; i < 2; ++i) {
-      const int32_t x = mem[i];
-      if (x < 0) continue;
-      cg.vw[c] += g.vw[x];
-      for (int64_t j = g.xadj[x]; j < g.xadj[x + 1]; ++j) {
-        const int32_t cv = cmap[g.adj[j]];
-        if (cv == c) continue;
-        if (slot[cv] < 0) {
-          slot[cv] = (int32_t)row.size();
-          row.emplace_back(cv, g.ew[j]);
-        } else {
-          row[slot[cv]].second += g.ew[j];
+  const int parts = loop_parts(nc);
+  std::vector<std::vector<int32_t>> padj(parts), pew(parts);
+  for_ranges(nc, parts, [&](int64_t lo, int64_t hi, int t) {
+    std::vector<std::pair<int32_t, int32_t>> row;
+    auto& oa = padj[t];
+    auto& ow = pew[t];
+    for (int64_t c = lo; c < hi; ++c) {
+      row.clear();
+      const int32_t mem[2] = {lead[c], other[c]};
+      int32_t w = 0;
+      for (int i = 0; i < 2; ++i) {
+        const int32_t x = mem[i];
+        if (x < 0) continue;
+        w += g.vw[x];
+        for (int64_t j = g.xadj[x]; j < g.xadj[x + 1]; ++j) {
+          const int32_t cv = cmap[g.adj[j]];
+          if (cv != (int32_t)c) row.emplace_back(cv, g.ew[j]);
         }
       }
+      cg.vw[c] = w;
+      std::sort(row.begin(), row.end());
+      int32_t len = 0;
+      for (size_t i = 0; i < row.size();) {
+        size_t j = i;
+        int32_t sum = 0;
+        while (j < row.size() && row[j].first == row[i].first) sum += row[j++].second;
+        oa.push_back(row[i].first);
+        ow.push_back(sum);
+        ++len;
+        i = j;
+      }
+      cg.xadj[c + 1] = len;
     }
-    std::sort(row.begin(), row.end());
-    for (auto& p : row) {
-      slot[p.first] = -1;
-      cg.adj.push_back(p.first);
-      cg.ew.push_back(p.second);
-    }
-    cg.xadj[c + 1] = (int64_t)cg.adj.size();
-  }
+  });
+  for (int32_t c = 0; c < nc; ++c) cg.xadj[c + 1] += cg.xadj[c];
+  cg.adj.resize(cg.xadj[nc]);
+  cg.ew.resize(cg.xadj[nc]);
+  for_ranges(parts, parts, [&](int64_t lo, int64_t, int t) {
+    const int64_t at = cg.xadj[(int64_t)nc * lo / parts];
+    std::copy(padj[t].begin(), padj[t].end(), cg.adj.begin() + at);
+    std::copy(pew[t].begin(), pew[t].end(), cg.ew.begin() + at);
+  });
 }
 
 // -------------------------------------------------------- initial bisection
@@ -228,13 +260,15 @@ void initial_cut(const Graph& g, int64_t sL, std::vector<uint8_t>& side) {
 inline int64_t iabs(int64_t a) { return a < 0 ? -a : a; }
 
 void gains_of(const Graph& g, const std::vector<uint8_t>& side, std::vector<int64_t>& gain) {
-  gain.assign(g.n, 0);
-  for (int32_t u = 0; u < g.n; ++u) {
-    int64_t ext = 0, in = 0;
-    for (int64_t j = g.xadj[u]; j < g.xadj[u + 1]; ++j)
-      (side[g.adj[j]] == side[u] ? in : ext) += g.ew[j];
-    gain[u] = ext - in;
-  }
+  gain.resize(g.n);
+  for_ranges(g.n, loop_parts(g.n), [&](int64_t lo, int64_t hi, int) {
+    for (int64_t u = lo; u < hi; ++u) {
+      int64_t ext = 0, in = 0;
+      for (int64_t j = g.xadj[u]; j < g.xadj[u + 1]; ++j)
+        (side[g.adj[j]] == side[u] ? in : ext) += g.ew[j];
+      gain[u] = ext - in;
+    }
+  });
 }
 
 void flip(const Graph& g, std::vector<uint8_t>& side, std::vector<int64_t>& gain, int32_t u) {
@@ -253,8 +287,8 @@ void refine_level(const Graph& g, int64_t sL, int64_t W, std::vector<uint8_t>& s
     if (!side[u]) lw += g.vw[u];
   std::vector<int64_t> gain;
   std::vector<int32_t> order;
+  gains_of(g, side, gain);  // kept exact by flip() across passes
   for (int pass = 0; pass < kPasses; ++pass) {
-    gains_of(g, side, gain);
     order.clear();
     for (int32_t u = 0; u < g.n; ++u)
       if (gain[u] > 0) order.push_back(u);
@@ -275,8 +309,9 @@ void refine_level(const Graph& g, int64_t sL, int64_t W, std::vector<uint8_t>& s
   }
 }
 
-// Exact balance at the finest level through a bucket queue keyed by gain;
-// each bucket keeps its ids ordered.
+// Exact balance at the finest level: a heap of (gain, -id) over the heavy
+// side, built in linear time and updated lazily (a vertex's gain only grows
+// while its neighbours leave, so older entries are recognisable as stale).
 void exact_balance(const Graph& g, int64_t sL, std::vector<uint8_t>& side) {
   int64_t lw = 0;
   for (int32_t u = 0; u < g.n; ++u)
@@ -285,26 +320,25 @@ void exact_balance(const Graph& g, int64_t sL, std::vector<uint8_t>& side) {
   const uint8_t heavy = lw > sL ? 0 : 1;
   std::vector<int64_t> gain;
   gains_of(g, side, gain);
-  std::map<int64_t, std::set<int32_t>> buckets;
+  using Item = std::pair<int64_t, int32_t>;  // (gain, -id): larger is better
+  std::vector<Item> heap;
+  heap.reserve((size_t)g.n);
   for (int32_t u = 0; u < g.n; ++u)
-    if (side[u] == heavy) buckets[gain[u]].insert(u);
-  while (lw != sL && !buckets.empty()) {
-    auto top = std::prev(buckets.end());
-    const int32_t u = *top->second.begin();
-    top->second.erase(top->second.begin());
-    if (top->second.empty()) buckets.erase(top);
-    // neighbours on the heavy side change bucket
-    for (int64_t j = g.xadj[u]; j < g.xadj[u + 1]; ++j) {
-      const int32_t x = g.adj[j];
-      if (side[x] != heavy) continue;
-      auto it = buckets.find(gain[x]);
-      it->second.erase(x);
-      if (it->second.empty()) buckets.erase(it);
-    }
+    if (side[u] == heavy) heap.emplace_back(gain[u], -u);
+  std::make_heap(heap.begin(), heap.end());
+  while (lw != sL && !heap.empty()) {
+    std::pop_heap(heap.begin(), heap.end());
+    const Item top = heap.back();
+    heap.pop_back();
+    const int32_t u = -top.second;
+    if (side[u] != heavy || top.first != gain[u]) continue;  // stale
     flip(g, side, gain, u);
     for (int64_t j = g.xadj[u]; j < g.xadj[u + 1]; ++j) {
       const int32_t x = g.adj[j];
-      if (side[x] == heavy) buckets[gain[x]].insert(x);
+      if (side[x] == heavy) {
+        heap.emplace_back(gain[x], -x);
+        std::push_heap(heap.begin(), heap.end());
+      }
     }
     lw += heavy ? 1 : -1;
   }
@@ -322,9 +356,11 @@ void bisect(const Graph& g0, int64_t sL, std::vector<uint8_t>& side) {
     if ((int64_t)nc * 10 > (int64_t)cur->n * 9) break;
     Graph cg;
     contract(*cur, cmap, lead, other, cg);
+    const bool dense = (int64_t)cg.adj.size() * 20 > (int64_t)cur->adj.size() * 17;
     maps.push_back(cmap);
     levels.push_back(std::move(cg));
     cur = &levels.back();
+    if (dense) break;  // the adjacency shrank by less than 15%: stop coarsening
   }
   initial_cut(*cur, sL, side);
   refine_level(*cur, sL, W, side);
