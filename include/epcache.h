@@ -234,8 +234,8 @@ int ep_set_threads(ep_schedule *s, int32_t threads);
  * schedule block (stage, compute, write back).  stages = 2..4 (default 3):
  * persistent CUDA blocks; a producer warp fills a ring of that many
  * shared-memory stages with 1-D TMA bulk copies of each schedule block's
- * contiguous pieces and pulls the block `ahead` positions later (0..64,
- * default 4) into L2; consumer warps (ep_set_threads) gather foreign records
+ * contiguous pieces and, with ahead > 0, a second warp pulls the block `ahead`
+ * positions later (0..64, default 0) into L2; consumer warps (ep_set_threads) gather foreign records
  * with cp.async and compute one stage while the next ones load.  Results
  * agree up to FP32 rounding order.
  */

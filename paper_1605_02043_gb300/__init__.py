@@ -179,7 +179,7 @@ class Schedule:
     def set_threads(self, threads: int):
         check(lib().ep_set_threads(self._h, threads))
 
-    def set_pipeline(self, stages: int, ahead: int = 4):
+    def set_pipeline(self, stages: int, ahead: int = 0):
         """0: one CUDA block per schedule block; 2..4: persistent pipelined kernel
         with `ahead` schedule blocks of L2 prefetch."""
         check(lib().ep_set_pipeline(self._h, stages, ahead))

@@ -140,7 +140,7 @@ struct ep_schedule {
   EventTimer timer;
   ep::dev::Timer* t() { return timer.on ? &timer : nullptr; }
   int stages = 3;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
-  int ahead = 4;   // L2 prefetch distance of the pipelined kernels, in schedule blocks per CUDA block
+  int ahead = 0;   // L2 prefetch distance of the pipelined kernels, in schedule blocks per CUDA block
   DBuf ws_ctl;     // [0] block counter, [1] error word
   int sm_count = 0;
   // launch plans of the pipelined kernels, cached per (D, adjoint) so that
