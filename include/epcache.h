@@ -41,6 +41,7 @@ extern "C" {
 #define EP_ECUDA (-3)    /* a CUDA runtime call failed (message has details) */
 #define EP_ETIMEOUT (-4) /* a bounded wait expired (device kernel or host thread) */
 #define EP_ENODEV (-5)   /* no CUDA device */
+#define EP_ECANCELED (-6) /* an asynchronous partition job was cancelled */
 
 /* ep_partition flags */
 #define EP_BIPARTITE 1u     /* SpMV graph: x_j -> vertex j, y_i -> vertex n+i */
@@ -54,6 +55,7 @@ extern "C" {
 #define EP_MAX_C 16384   /* block capacity limit (local indices are 16-bit) */
 
 typedef struct ep_schedule ep_schedule; /* opaque, library-owned */
+typedef struct ep_job ep_job;           /* opaque: an asynchronous partition */
 
 /* Library version (major*10000 + minor*100 + patch). */
 int ep_version(void);
@@ -79,6 +81,40 @@ const char *ep_last_error(void);
  */
 int ep_partition(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, int32_t C,
                  uint32_t flags, int32_t threads, ep_schedule **out);
+
+/*
+ * Asynchronous partition: the optimisation thread of Section 4.2, which
+ * partitions while the application keeps running its kernel under the
+ * default schedule, and is stopped if the application ends first.
+ * ep_partition_start checks its arguments like ep_partition, copies src and
+ * dst (the caller may free them on return) and starts one host thread that
+ * runs ep_partition on the copies; the result is bit-identical to
+ * ep_partition's.  Test hooks (host-side fault injection, no GPU involved):
+ * flags | EP_JOB_TEST_FAIL makes the job fail at once with EP_ENOMEM;
+ * flags | EP_JOB_TEST_HOLD makes it do nothing until cancelled (after 60 s
+ * it ends by itself with EP_ETIMEOUT).
+ *   ep_job_wait    waits up to timeout_ms (0: poll, < 0: no limit); *done = 1
+ *                  once the job has ended (finished, failed or cancelled).
+ *   ep_job_take    after the end: hands over the schedule (*out, to be freed
+ *                  with ep_schedule_free) and the job's wall time in seconds
+ *                  (*seconds, may be NULL); returns the job's own error code
+ *                  (EP_ECANCELED, EP_ENOMEM, ...) if it failed, EP_EINVAL if
+ *                  it is still running or the schedule was already taken.
+ *   ep_job_cancel  asks the job to stop; the partitioner checks the request
+ *                  between coarsening levels and between bisections, so the
+ *                  job ends soon after with EP_ECANCELED.
+ *   ep_job_free    cancels, joins the thread and frees everything not taken.
+ * A job may be waited on from several threads; ep_job_free must be the last
+ * call on it.
+ */
+#define EP_JOB_TEST_FAIL 0x100u
+#define EP_JOB_TEST_HOLD 0x200u
+int ep_partition_start(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, int32_t C,
+                       uint32_t flags, int32_t threads, ep_job **out);
+int ep_job_wait(ep_job *job, int64_t timeout_ms, int32_t *done);
+int ep_job_take(ep_job *job, ep_schedule **out, double *seconds);
+int ep_job_cancel(ep_job *job);
+int ep_job_free(ep_job *job);
 
 /* Sizes of a schedule.  nd = number of data vertices (n, or 2n if bipartite).
  * Any output pointer may be NULL. */
@@ -234,10 +270,10 @@ int ep_set_threads(ep_schedule *s, int32_t threads);
  * schedule block (stage, compute, write back).  stages = 2..4 (default 3):
  * persistent CUDA blocks; a producer warp fills a ring of that many
  * shared-memory stages with 1-D TMA bulk copies of each schedule block's
- * contiguous pieces and, with ahead > 0, a second warp pulls the block `ahead`
- * positions later (0..64, default 0) into L2; consumer warps (ep_set_threads) gather foreign records
- * with cp.async and compute one stage while the next ones load.  Results
- * agree up to FP32 rounding order.
+ * contiguous pieces; with ahead > 0 (0..64, default 0) a second warp pulls
+ * the schedule block `ahead` positions later into L2; consumer warps
+ * (ep_set_threads) gather foreign records with cp.async and compute one
+ * stage while the next ones load.  Results agree up to FP32 rounding order.
  */
 int ep_set_pipeline(ep_schedule *s, int32_t stages, int32_t ahead);
 
@@ -248,6 +284,17 @@ int ep_set_pipeline(ep_schedule *s, int32_t stages, int32_t ahead);
  * free stage).  *code = 0 and EP_OK when clean, else EP_ETIMEOUT.
  */
 int ep_check_errors(ep_schedule *s, int32_t *code, void *stream);
+
+/*
+ * Test hook for the bounded waits (no counterpart in the paper).  With
+ * block_index >= 0, the producer of every persistent CUDA block leaves the
+ * stage of its block_index-th schedule block unfilled (nothing copied,
+ * nothing arrives), so the consumers' bounded wait for it expires: the
+ * launch returns early with bit 0 set in the error word, its results are
+ * invalid, and ep_check_errors() reports EP_ETIMEOUT and resets the
+ * accumulators.  -1 (default) turns the hook off.
+ */
+int ep_debug_stall(ep_schedule *s, int32_t block_index);
 
 void ep_schedule_free(ep_schedule *s);
 

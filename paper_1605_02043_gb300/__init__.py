@@ -13,13 +13,15 @@ import numpy as np
 
 from ._lib import EpError, check, lib
 
-__all__ = ["Schedule", "EpError", "FLUX", "SPMV", "BIPARTITE", "DEFAULT_ORDER", "record_floats",
+__all__ = ["Schedule", "PartitionJob", "EpError", "FLUX", "SPMV", "BIPARTITE", "DEFAULT_ORDER", "record_floats",
            "T_EDGE_FWD", "T_BND", "T_EDGE_ADJ", "T_SPMV", "T_LAYOUT", "T_COST"]
 
 FLUX = 0
 SPMV = 1
 BIPARTITE = 1
 DEFAULT_ORDER = 2
+JOB_TEST_FAIL = 0x100  # test hooks of ep_partition_start (host-side fault injection)
+JOB_TEST_HOLD = 0x200
 # kernel classes of Schedule.timing_read (EP_T_* in epcache.h)
 T_EDGE_FWD, T_BND, T_EDGE_ADJ, T_SPMV, T_LAYOUT, T_COST = range(6)
 
@@ -50,6 +52,14 @@ def _need_cuda_f32(t, name, numel=None):
         raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
 
 
+def _edges(src, dst):
+    src = np.ascontiguousarray(src, np.int32)
+    dst = np.ascontiguousarray(dst, np.int32)
+    if src.shape != dst.shape or src.ndim != 1:
+        raise ValueError("src and dst must be equal-length 1-D arrays")
+    return src, dst
+
+
 def record_floats(D: int) -> int:
     return int(lib().ep_record_floats(D))
 
@@ -70,10 +80,7 @@ class Schedule:
     @classmethod
     def partition(cls, src, dst, n: int, C: int, bipartite: bool = False,
                   default_order: bool = False, threads: int = 0) -> "Schedule":
-        src = np.ascontiguousarray(src, np.int32)
-        dst = np.ascontiguousarray(dst, np.int32)
-        if src.shape != dst.shape or src.ndim != 1:
-            raise ValueError("src and dst must be equal-length 1-D arrays")
+        src, dst = _edges(src, dst)
         flags = (BIPARTITE if bipartite else 0) | (DEFAULT_ORDER if default_order else 0)
         h = ctypes.c_void_p()
         check(lib().ep_partition(src.ctypes.data, dst.ctypes.data, src.size, n, C, flags, threads,
@@ -190,6 +197,10 @@ class Schedule:
         check(lib().ep_check_errors(self._h, ctypes.byref(code), _stream(stream)))
         return code.value
 
+    def debug_stall(self, block_index: int):
+        """Test hook: make the pipelined kernels' bounded waits expire (-1 turns it off)."""
+        check(lib().ep_debug_stall(self._h, block_index))
+
     def timing(self, enable: int = 2):
         """Start (2 = clear and start), keep (1) or stop (0) per-kernel timing."""
         check(lib().ep_timing(self._h, enable))
@@ -237,3 +248,54 @@ class Schedule:
     def adjoint_step(self, D: int, x_lay, w_lay, lam, grad_w_lay, tau: float = 1e-3, stream=None):
         check(lib().ep_adjoint_step(self._h, D, _vp(x_lay), _vp(w_lay), _vp(lam), _vp(grad_w_lay),
                                     tau, _stream(stream)))
+
+
+class PartitionJob:
+    """Schedule.partition on a library-owned host thread (ep_partition_start).
+
+    The optimisation thread of Section 4.2: the caller keeps launching its
+    kernel under another schedule and polls; ``cancel`` stops the partitioner
+    between bisections.  ``test`` takes JOB_TEST_FAIL or JOB_TEST_HOLD.
+    """
+
+    def __init__(self, src, dst, n: int, C: int, bipartite: bool = False, threads: int = 0,
+                 test: int = 0):
+        src, dst = _edges(src, dst)
+        flags = (BIPARTITE if bipartite else 0) | test
+        self._h = ctypes.c_void_p()
+        check(lib().ep_partition_start(src.ctypes.data, dst.ctypes.data, src.size, n, C, flags,
+                                       threads, ctypes.byref(self._h)))
+        self.seconds = None
+
+    def wait(self, timeout: float | None = None) -> bool:
+        """True once the job has ended; timeout in seconds (0 polls, None waits)."""
+        done = ctypes.c_int32()
+        ms = -1 if timeout is None else int(round(timeout * 1000))
+        check(lib().ep_job_wait(self._h, ms, ctypes.byref(done)))
+        return bool(done.value)
+
+    def done(self) -> bool:
+        return self.wait(0)
+
+    def take(self) -> Schedule:
+        """The finished schedule; raises EpError with the job's code if it failed."""
+        h = ctypes.c_void_p()
+        sec = ctypes.c_double()
+        rc = lib().ep_job_take(self._h, ctypes.byref(h), ctypes.byref(sec))
+        self.seconds = sec.value if rc != -1 else None
+        check(rc)
+        return Schedule(h)
+
+    def cancel(self):
+        check(lib().ep_job_cancel(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ep_job_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

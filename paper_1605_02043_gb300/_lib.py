@@ -21,6 +21,11 @@ SIGNATURES = {
     "ep_version": (ctypes.c_int, []),
     "ep_last_error": (ctypes.c_char_p, []),
     "ep_partition": (ctypes.c_int, [P, P, I64, I64, I32, U32, I32, ctypes.POINTER(P)]),
+    "ep_partition_start": (ctypes.c_int, [P, P, I64, I64, I32, U32, I32, ctypes.POINTER(P)]),
+    "ep_job_wait": (ctypes.c_int, [P, I64, P]),
+    "ep_job_take": (ctypes.c_int, [P, ctypes.POINTER(P), P]),
+    "ep_job_cancel": (ctypes.c_int, [P]),
+    "ep_job_free": (ctypes.c_int, [P]),
     "ep_schedule_info": (ctypes.c_int, [P, P, P, P, P, P, P]),
     "ep_schedule_arrays": (ctypes.c_int, [P, P, P, P, P, P]),
     "ep_cost_host": (ctypes.c_int, [P, P, P]),
@@ -46,6 +51,7 @@ SIGNATURES = {
     "ep_set_threads": (ctypes.c_int, [P, I32]),
     "ep_set_pipeline": (ctypes.c_int, [P, I32, I32]),
     "ep_check_errors": (ctypes.c_int, [P, P, P]),
+    "ep_debug_stall": (ctypes.c_int, [P, I32]),
     "ep_schedule_free": (None, [P]),
     "ep_cost_noalloc": (ctypes.c_int, [P, P, P, I64, I64, I32, P, P]),
     "ep_noalloc_last_error": (ctypes.c_char_p, []),

@@ -2,9 +2,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -141,6 +145,7 @@ struct ep_schedule {
   ep::dev::Timer* t() { return timer.on ? &timer : nullptr; }
   int stages = 3;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
   int ahead = 0;   // L2 prefetch distance of the pipelined kernels, in schedule blocks per CUDA block
+  int stall = -1;  // test hook of the bounded waits (ep_debug_stall)
   DBuf ws_ctl;     // [0] block counter, [1] error word
   int sm_count = 0;
   // launch plans of the pipelined kernels, cached per (D, adjoint) so that
@@ -245,7 +250,7 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
 // Stage layout and grid of the pipelined kernels for state width D (cached;
 // recomputed when the stage count, look-ahead or thread count changes).
 int tma_plan(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
-  const int key = 1 + s->stages + 8 * s->ahead + 1024 * s->tpb;
+  const int key = 1 + s->stages + 8 * s->ahead + 1024 * s->tpb + (1 << 22) * (s->stall + 1);
   if (s->plan_key[D][adjoint] != key) {
     if (int rc = tma_plan_compute(s, D, adjoint, s->plans[D][adjoint])) return rc;
     s->plan_key[D][adjoint] = key;
@@ -277,6 +282,7 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
   CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   L.stages = std::min(s->stages, ep::dev::kMaxStages);
   L.ahead = s->ahead;
+  L.stall = s->stall;
   optin -= 1024;  // room for the kernel's static shared memory
   while (L.stages > 2 && (int64_t)L.stages * L.stage_bytes > optin) --L.stages;
   if ((int64_t)L.stages * L.stage_bytes > optin)
@@ -426,6 +432,102 @@ int new_schedule(ep_schedule** out, ep_schedule** holder) {
   return EP_OK;
 }
 
+int check_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t C,
+                uint32_t flags) {
+  if (!src || !dst) return fail(EP_EINVAL, "null edge arrays");
+  if (m <= 0 || m >= INT32_MAX) return fail(EP_EINVAL, "m = %lld out of range", (long long)m);
+  if (n <= 0 || n >= INT32_MAX / 2) return fail(EP_EINVAL, "n = %lld out of range", (long long)n);
+  if (C < 1 || C > EP_MAX_C) return fail(EP_EINVAL, "C = %d out of [1, %d]", C, EP_MAX_C);
+  if (flags & ~(EP_BIPARTITE | EP_DEFAULT_ORDER)) return fail(EP_EINVAL, "unknown flags");
+  for (int64_t e = 0; e < m; ++e)
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
+      return fail(EP_EINVAL, "task %lld uses a vertex outside [0, %lld)", (long long)e, (long long)n);
+  return EP_OK;
+}
+
+// Partition (Section 3) and build the schedule into s.  A raised *stop ends
+// the work early with EP_ECANCELED.
+int fill_partition(ep_schedule* s, const int32_t* src, const int32_t* dst, int64_t m, int64_t n,
+                   int32_t C, uint32_t flags, int threads, const std::atomic<int>* stop) {
+  try {
+    ep::HostSchedule& h = s->h;
+    h.m = m;
+    h.n = n;
+    h.nd = (flags & EP_BIPARTITE) ? 2 * n : n;
+    h.C = C;
+    h.flags = flags;
+    h.k = (m + C - 1) / C;
+    h.src.assign(src, src + m);
+    h.dst.assign(dst, dst + m);
+    h.part.resize(m);
+    if (!ep::partition_edges(src, dst, m, n, C, flags, threads, h.part.data(), stop))
+      return fail(EP_ECANCELED, "partition cancelled");
+    if (stop && stop->load()) return fail(EP_ECANCELED, "partition cancelled");
+    std::string err = ep::build_schedule(h, threads);
+    if (!err.empty()) return fail(EP_EINVAL, "%s", err.c_str());
+  } catch (const std::bad_alloc&) {
+    return fail(EP_ENOMEM, "out of host memory");
+  }
+  return EP_OK;
+}
+
+}  // namespace
+
+// Asynchronous partition (the optimisation thread of Section 4.2).
+struct ep_job {
+  std::vector<int32_t> src, dst;  // private copies of the edge list
+  int64_t m = 0, n = 0;
+  int32_t C = 0, threads = 0;
+  uint32_t flags = 0, test = 0;
+  std::atomic<int> stop{0};
+  std::mutex mu;
+  std::condition_variable cv;
+  bool done = false;  // guarded by mu, like the fields below
+  int rc = EP_OK;
+  std::string msg;
+  ep_schedule* result = nullptr;
+  double seconds = 0;
+  std::thread th;
+};
+
+namespace {
+
+constexpr int kHoldSeconds = 60;  // a held test job gives up after this long
+
+void job_main(ep_job* j) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int rc = EP_OK;
+  std::string msg;
+  ep_schedule* s = nullptr;
+  if (j->test & EP_JOB_TEST_FAIL) {
+    rc = EP_ENOMEM;
+    msg = "injected failure";
+  } else if (j->test & EP_JOB_TEST_HOLD) {
+    std::unique_lock<std::mutex> lk(j->mu);
+    const bool stop = j->cv.wait_for(lk, std::chrono::seconds(kHoldSeconds),
+                                     [&] { return j->stop.load() != 0; });
+    rc = stop ? EP_ECANCELED : EP_ETIMEOUT;
+    msg = stop ? "partition cancelled" : "held test job timed out";
+  } else if ((rc = new_schedule(nullptr, &s)) == EP_OK) {
+    rc = fill_partition(s, j->src.data(), j->dst.data(), j->m, j->n, j->C, j->flags, j->threads,
+                        &j->stop);
+    if (rc != EP_OK) {
+      delete s;
+      s = nullptr;
+    }
+  }
+  if (rc != EP_OK && msg.empty()) msg = g_error;
+  {
+    std::lock_guard<std::mutex> lk(j->mu);
+    j->rc = rc;
+    j->msg = msg;
+    j->result = s;
+    j->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    j->done = true;
+  }
+  j->cv.notify_all();
+}
+
 }  // namespace
 
 extern "C" {
@@ -439,38 +541,88 @@ int ep_partition(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, i
   g_error.clear();
   if (!out) return fail(EP_EINVAL, "null output pointer");
   *out = nullptr;
-  if (!src || !dst) return fail(EP_EINVAL, "null edge arrays");
-  if (m <= 0 || m >= INT32_MAX) return fail(EP_EINVAL, "m = %lld out of range", (long long)m);
-  if (n <= 0 || n >= INT32_MAX / 2) return fail(EP_EINVAL, "n = %lld out of range", (long long)n);
-  if (C < 1 || C > EP_MAX_C) return fail(EP_EINVAL, "C = %d out of [1, %d]", C, EP_MAX_C);
-  if (flags & ~(EP_BIPARTITE | EP_DEFAULT_ORDER)) return fail(EP_EINVAL, "unknown flags");
-  for (int64_t e = 0; e < m; ++e)
-    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
-      return fail(EP_EINVAL, "task %lld uses a vertex outside [0, %lld)", (long long)e, (long long)n);
+  if (int rc = check_edges(src, dst, m, n, C, flags)) return rc;
   ep_schedule* s = nullptr;
   if (int rc = new_schedule(out, &s)) return rc;
-  try {
-    ep::HostSchedule& h = s->h;
-    h.m = m;
-    h.n = n;
-    h.nd = (flags & EP_BIPARTITE) ? 2 * n : n;
-    h.C = C;
-    h.flags = flags;
-    h.k = (m + C - 1) / C;
-    h.src.assign(src, src + m);
-    h.dst.assign(dst, dst + m);
-    h.part.resize(m);
-    ep::partition_edges(src, dst, m, n, C, flags, threads, h.part.data());
-    std::string err = ep::build_schedule(h, threads);
-    if (!err.empty()) {
-      delete s;
-      return fail(EP_EINVAL, "%s", err.c_str());
-    }
-  } catch (const std::bad_alloc&) {
+  if (int rc = fill_partition(s, src, dst, m, n, C, flags, threads, nullptr)) {
     delete s;
-    return fail(EP_ENOMEM, "out of host memory");
+    return rc;
   }
   *out = s;
+  return EP_OK;
+}
+
+int ep_partition_start(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t C,
+                       uint32_t flags, int32_t threads, ep_job** out) {
+  g_error.clear();
+  if (!out) return fail(EP_EINVAL, "null output pointer");
+  *out = nullptr;
+  const uint32_t test = flags & (EP_JOB_TEST_FAIL | EP_JOB_TEST_HOLD);
+  flags &= ~test;
+  if (int rc = check_edges(src, dst, m, n, C, flags)) return rc;
+  ep_job* j = new (std::nothrow) ep_job();
+  if (!j) return fail(EP_ENOMEM, "out of host memory");
+  try {
+    j->src.assign(src, src + m);
+    j->dst.assign(dst, dst + m);
+    j->m = m;
+    j->n = n;
+    j->C = C;
+    j->flags = flags;
+    j->threads = threads;
+    j->test = test;
+    j->th = std::thread(job_main, j);
+  } catch (const std::exception&) {
+    delete j;
+    return fail(EP_ENOMEM, "could not start the partition thread");
+  }
+  *out = j;
+  return EP_OK;
+}
+
+int ep_job_wait(ep_job* j, int64_t timeout_ms, int32_t* done) {
+  g_error.clear();
+  if (!j || !done) return fail(EP_EINVAL, "null argument");
+  std::unique_lock<std::mutex> lk(j->mu);
+  if (timeout_ms < 0)
+    j->cv.wait(lk, [&] { return j->done; });
+  else if (timeout_ms > 0)
+    j->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return j->done; });
+  *done = j->done ? 1 : 0;
+  return EP_OK;
+}
+
+int ep_job_take(ep_job* j, ep_schedule** out, double* seconds) {
+  g_error.clear();
+  if (!j || !out) return fail(EP_EINVAL, "null argument");
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(j->mu);
+  if (!j->done) return fail(EP_EINVAL, "the partition job is still running");
+  if (seconds) *seconds = j->seconds;
+  if (j->rc != EP_OK) return fail(j->rc, "partition job: %s", j->msg.c_str());
+  if (!j->result) return fail(EP_EINVAL, "the schedule was already taken");
+  *out = j->result;
+  j->result = nullptr;
+  return EP_OK;
+}
+
+int ep_job_cancel(ep_job* j) {
+  g_error.clear();
+  if (!j) return fail(EP_EINVAL, "null job");
+  {
+    std::lock_guard<std::mutex> lk(j->mu);
+    j->stop.store(1);
+  }
+  j->cv.notify_all();
+  return EP_OK;
+}
+
+int ep_job_free(ep_job* j) {
+  if (!j) return EP_OK;
+  ep_job_cancel(j);
+  if (j->th.joinable()) j->th.join();
+  delete j->result;
+  delete j;
   return EP_OK;
 }
 
@@ -838,8 +990,16 @@ int ep_check_errors(ep_schedule* s, int32_t* code, void* stream) {
   *code = v[1];
   if (v[1]) {
     CU(cudaMemsetAsync(s->ws_ctl.as<int>() + 1, 0, sizeof(int), st));
+    s->bacc_dirty = true;  // an interrupted launch may have left partial sums
     return fail(EP_ETIMEOUT, "a pipelined kernel gave up waiting (code %d)", v[1]);
   }
+  return EP_OK;
+}
+
+int ep_debug_stall(ep_schedule* s, int32_t block_index) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (block_index < -1 || block_index > 255) return fail(EP_EINVAL, "block_index = %d", block_index);
+  s->stall = block_index;
   return EP_OK;
 }
 

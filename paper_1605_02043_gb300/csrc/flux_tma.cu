@@ -371,6 +371,7 @@ __device__ __forceinline__ void pipeline(const FluxDesc* __restrict__ desc,
         mbar_arrive(&full[s]);
         return;
       }
+      if (j == L.stall) return;  // test hook: this stage is never filled
       const FluxDesc d = dn;
       if (b + G < k) dn = desc[b + G];  // next descriptor in flight while copying this one
       produce<D>(d, (int)b, flist, inc, ptr, w, x, ADJ ? lam : nullptr, n_rec, S, L, &full[s]);

@@ -1,6 +1,7 @@
 // internal.h -- shared declarations of libepcache (not part of the C ABI).
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -94,8 +95,10 @@ struct HostSchedule {
 };
 
 // partition.cpp
-void partition_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t C,
-                     uint32_t flags, int threads, int32_t* part);
+// Returns false (part unfinished) when *stop became non-zero during the run.
+bool partition_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t C,
+                     uint32_t flags, int threads, int32_t* part,
+                     const std::atomic<int>* stop = nullptr);
 
 // schedule.cpp: everything after the partition (Definition 4, vertex lists,
 // cpack, cost, kernel layout).  Returns an empty string or an error message.

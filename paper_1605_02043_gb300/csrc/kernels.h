@@ -73,6 +73,7 @@ struct TmaLayout {
   int stage_bytes;
   int stages;
   int ahead;  // schedule blocks of look-ahead for L2 prefetch (0: none)
+  int stall;  // test hook: leave the stage of this block index unfilled (-1: off)
 };
 struct TmaPlan {
   TmaLayout L;

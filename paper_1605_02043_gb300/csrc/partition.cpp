@@ -344,7 +344,12 @@ void exact_balance(const Graph& g, int64_t sL, std::vector<uint8_t>& side) {
   }
 }
 
-void bisect(const Graph& g0, int64_t sL, std::vector<uint8_t>& side) {
+bool stopped(const std::atomic<int>* stop) {
+  return stop && stop->load(std::memory_order_relaxed) != 0;
+}
+
+// Leaves `side` unfinished when `stop` is raised (the caller checks it too).
+void bisect(const Graph& g0, int64_t sL, std::vector<uint8_t>& side, const std::atomic<int>* stop) {
   const int64_t W = g0.n;
   const int32_t maxw = (int32_t)std::max<int64_t>(1, std::min(sL, W - sL) / 16);
   std::vector<Graph> levels;  // coarse levels 1..L
@@ -352,6 +357,7 @@ void bisect(const Graph& g0, int64_t sL, std::vector<uint8_t>& side) {
   const Graph* cur = &g0;
   std::vector<int32_t> cmap, lead, other;
   while (cur->n > kCoarsenMin && levels.size() < 63) {
+    if (stopped(stop)) return;
     const int32_t nc = heavy_edge_matching(*cur, maxw, cmap, lead, other);
     if ((int64_t)nc * 10 > (int64_t)cur->n * 9) break;
     Graph cg;
@@ -365,6 +371,7 @@ void bisect(const Graph& g0, int64_t sL, std::vector<uint8_t>& side) {
   initial_cut(*cur, sL, side);
   refine_level(*cur, sL, W, side);
   for (int l = (int)levels.size() - 1; l >= 0; --l) {
+    if (stopped(stop)) return;
     const Graph& fine = l == 0 ? g0 : levels[l - 1];
     std::vector<uint8_t> fs(fine.n);
     for (int32_t u = 0; u < fine.n; ++u) fs[u] = side[maps[l][u]];
@@ -404,18 +411,21 @@ struct Recursion {
   int32_t C;
   int32_t* part;
   std::atomic<int> spare;  // threads that may still be started
+  const std::atomic<int>* stop;  // cancellation request (nullable)
 };
 
 constexpr int32_t kSpawnMin = 4096;  // do not start a thread for smaller subtrees
 
 void recurse(Graph g, std::vector<int32_t> gid, int32_t kk, int32_t first, Recursion& R) {
+  if (stopped(R.stop)) return;
   if (kk == 1) {
     for (int32_t x : gid) R.part[x] = first;
     return;
   }
   const int32_t kL = (kk + 1) / 2;
   std::vector<uint8_t> side;
-  bisect(g, (int64_t)kL * R.C, side);
+  bisect(g, (int64_t)kL * R.C, side, R.stop);
+  if (stopped(R.stop)) return;
   Graph gl, gr;
   std::vector<int32_t> il, ir;
   split(g, gid, side, 0, gl, il);
@@ -442,12 +452,12 @@ void recurse(Graph g, std::vector<int32_t> gid, int32_t kk, int32_t first, Recur
 
 }  // namespace
 
-void partition_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t C,
-                     uint32_t flags, int threads, int32_t* part) {
+bool partition_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t C,
+                     uint32_t flags, int threads, int32_t* part, const std::atomic<int>* stop) {
   const int32_t k = (int32_t)((m + C - 1) / C);
   if ((flags & 2u) || k == 1) {
     for (int64_t e = 0; e < m; ++e) part[e] = (int32_t)(e / C);
-    return;
+    return true;
   }
   Graph H;
   build_h(src, dst, m, n, (flags & 1u) != 0, H);
@@ -458,7 +468,9 @@ void partition_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t 
   R.C = C;
   R.part = part;
   R.spare.store(threads - 1);
+  R.stop = stop;
   recurse(std::move(H), std::move(gid), k, 0, R);
+  return !stopped(stop);
 }
 
 }  // namespace ep

@@ -120,6 +120,13 @@ def test_invalid_arguments():
     h = ctypes.c_void_p()
     assert _lib.lib().ep_partition(src.ctypes.data, dst.ctypes.data, 3, 4, 2, 8, 0,
                                    ctypes.byref(h)) == -1  # unknown flag
+    S = E.Schedule.partition(src, dst, 4, 2)
+    for bad in (-2, 256):
+        with pytest.raises(E.EpError) as ei:
+            S.debug_stall(bad)
+        assert ei.value.code == -1
+    S.debug_stall(0)
+    S.debug_stall(-1)
 
 
 def test_kernel_calls_need_a_device():
