@@ -16,7 +16,8 @@ Reported (one JSON line on rank 0):
                included) through the autograd function, edge updates/s
   roofline     the forward edge kernel: algorithmic bytes per launch (the cost
                model of Eq. 1, 4*D bytes per vertex load) / its mean duration
-  e2e          ep_run_host: host x, w in pinned memory, 100 steps, x back
+  e2e          ep_run_host with one step per call: host x, w (pinned) copied in
+               and x read back every step; resident_state = 100 steps per call
   cpu_baseline the FP64 oracle on the host, bounded sample of steps
 With --impl reference the oracle itself is timed as the reference arm.
 """
@@ -61,6 +62,9 @@ def parse():
                     help="mesh: 1M-node kNN mesh flux steps; rmat: R-MAT scale-20 SpMV; "
                          "batch: 512 uneven meshes, 100 steps fwd+bwd in one CUDA graph")
     ap.add_argument("--meshes", type=int, default=512, help="batch workload: number of meshes")
+    ap.add_argument("--study", default="", choices=["", "cache"],
+                    help="cache: shared-memory staging vs read-only data cache, C in {256, 512, 1024}, "
+                         "partitioned and default schedules (one JSON line, no bench line)")
     return ap.parse_args()
 
 
@@ -222,20 +226,34 @@ def bench_fwd_bwd(torch, S, x0, w, iters, warmup, flush, T=10, every=5):
     return dict(ms=ms, T=T)
 
 
-def bench_e2e(torch, S, x0, w, reps=3, T=100):
+def bench_e2e(torch, S, x0, w, reps=20, T_long=100):
+    """End to end through the public host-buffer call (ep_run_host): every step
+    copies that step's inputs (state and weights, pinned host memory) to the
+    device and reads the new state back.  Also reported: the same call running
+    T_long steps per copy-in/copy-out (state resident between steps)."""
     xh = torch.from_numpy(x0.copy()).pin_memory()
     wh = torch.from_numpy(w.copy()).pin_memory()
-    S.run_host(xh, wh, None, steps=T, tau=TAU, D=D)  # warm-up (allocates workspace)
+    for _ in range(3):  # warm-up (allocates workspace)
+        S.run_host(xh, wh, None, steps=1, tau=TAU, D=D)
     barrier(torch)
     times = []
     for _ in range(reps):
-        xh.copy_(torch.from_numpy(x0))
         t0 = time.perf_counter()
-        S.run_host(xh, wh, None, steps=T, tau=TAU, D=D)
+        S.run_host(xh, wh, None, steps=1, tau=TAU, D=D)
         times.append(time.perf_counter() - t0)
     t = max_over_ranks(torch, statistics.median(times))
-    return dict(value=S.m * T / t, unit=UNIT, h2d_bytes_per_step=int(xh.numel() * 4 + wh.numel() * 4),
-                d2h_bytes_per_step=int(xh.numel() * 4), steps_per_call=T, seconds_per_call=t)
+    long_times = []
+    for _ in range(3):
+        xh.copy_(torch.from_numpy(x0))
+        t0 = time.perf_counter()
+        S.run_host(xh, wh, None, steps=T_long, tau=TAU, D=D)
+        long_times.append(time.perf_counter() - t0)
+    tl = max_over_ranks(torch, statistics.median(long_times))
+    return dict(value=S.m / t, unit=UNIT, h2d_bytes_per_step=int(xh.numel() * 4 + wh.numel() * 4),
+                d2h_bytes_per_step=int(xh.numel() * 4), steps_per_call=1, seconds_per_step=t,
+                resident_state={"steps_per_call": T_long, "value": S.m * T_long / tl, "unit": UNIT,
+                                "h2d_bytes_per_call": int(xh.numel() * 4 + wh.numel() * 4),
+                                "d2h_bytes_per_call": int(xh.numel() * 4)})
 
 
 def cpu_baseline(src, dst, x0, w, seconds):
@@ -254,6 +272,44 @@ def cpu_baseline(src, dst, x0, w, seconds):
                 sample=f"{steps} FP64 NumPy flux steps of the full mesh ({src.size} tasks), single thread")
 
 
+def spmv_time(torch, E, sch, x0, w, n, steps, warmup, flush):
+    """Mean SpMV kernel time (ms) and step time (ms) on schedule-layout buffers."""
+    xl = torch.empty(n, device="cuda")
+    wl = torch.empty(sch.weights_floats(), device="cuda")
+    yl = torch.empty(n, device="cuda")
+    sch.spmv_x_in(torch.from_numpy(x0).cuda(), xl)
+    sch.weights_in(torch.from_numpy(w).cuda(), wl)
+    for _ in range(warmup):
+        sch.spmv(xl, wl, yl)
+    sch.timing(2)
+    ms = timed_loop(torch, lambda: sch.spmv(xl, wl, yl), steps, 0, flush)
+    kms, kn = sch.timing_read(E.T_SPMV)
+    sch.timing(0)
+    return kms / max(kn, 1), statistics.mean(ms)
+
+
+def study_cache_spmv(torch, E, args, rows, cols, n, x0, w):
+    """EP-smem vs EP-text (Section 5, Fig. 11, Table 3) for the R-MAT SpMV."""
+    flush = L2Flush(torch)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    out = []
+    for C in (256, 512, 1024):
+        for sched, dflt in (("partitioned", False), ("default", True)):
+            S = E.Schedule.partition(rows, cols, n, C, bipartite=True, default_order=dflt)
+            S.set_threads(args.threads)
+            loads, _ = S.cost_host()
+            for name, mode in (("smem", E.CACHE_SMEM), ("l1_readonly", E.CACHE_L1)):
+                S.set_cache(mode)
+                kms, sms = spmv_time(torch, E, S, x0, w, n, max(20, args.steps // 5), args.warmup, flush)
+                out.append(dict(C=C, schedule=sched, kernel=name, loads=loads, kernel_us=1e3 * kms,
+                                step_us=1e3 * sms, edge_updates_per_s=rows.size / (1e-3 * sms)))
+            S.close()
+    clk = clocks.stop()
+    print(json.dumps({"study": "cache", "workload": "rmat", "n": n, "m": int(rows.size),
+                      "threads": args.threads, "rows": out, "clocks": clk}))
+
+
 def bench_rmat(args):
     """SpMV on the R-MAT scale-20 graph (y_u += w_e x_v), partitioned vs default order."""
     import torch
@@ -267,6 +323,9 @@ def bench_rmat(args):
     rows, cols = W.rmat()
     n, m = 1 << 20, rows.size
     x0, w = W.spmv_inputs(n, m, 0)
+    if args.study == "cache":
+        study_cache_spmv(torch, E, args, rows, cols, n, x0, w)
+        return
     C = args.C if args.C != 256 else 512
     t0 = time.perf_counter()
     S = E.Schedule.partition(rows, cols, n, C, bipartite=True)
@@ -476,6 +535,31 @@ def run_reference(args):
     }))
 
 
+def study_cache(torch, E, args, src, dst, x0, w, flush):
+    """Texture-cache vs software-cache study of Section 5 (Fig. 11, Table 3) on
+    GB300: forward edge-kernel time per launch and step time, per C and schedule."""
+    n, m = args.n, src.size
+    kinds = (("smem_pipelined", E.CACHE_SMEM, args.stages or 3),
+             ("smem_block", E.CACHE_SMEM, 0),
+             ("l1_readonly", E.CACHE_L1, 0))
+    rows = []
+    for C in (256, 512, 1024):
+        for sched, default_order in (("partitioned", False), ("default", True)):
+            S = E.Schedule.partition(src, dst, n, C, default_order=default_order)
+            S.set_threads(args.threads)
+            loads, _ = S.cost_host()
+            for name, cache, stages in kinds:
+                S.set_pipeline(stages)
+                S.set_cache(cache)
+                r = bench_fwd(torch, E, S, x0, w, max(20, args.steps // 5), args.warmup, flush)
+                rows.append(dict(C=C, schedule=sched, kernel=name, loads=loads,
+                                 edge_kernel_us=1e3 * r["edge_ms"], bnd_kernel_us=1e3 * r["bnd_ms"],
+                                 step_us=1e3 * statistics.mean(r["ms"]),
+                                 edge_updates_per_s=m * len(r["ms"]) / (1e-3 * sum(r["ms"]))))
+            S.close()
+    return rows
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -512,6 +596,13 @@ def main():
 
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
+    if args.study == "cache":
+        rows = study_cache(torch, E, args, src, dst, x0, w, flush)
+        clk = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"study": "cache", "n": n, "m": m, "D": D, "threads": args.threads,
+                              "rows": rows, "clocks": clk}))
+        return
     fwd = bench_fwd(torch, E, S, x0, w, args.steps, args.warmup, flush)
     fwd_d = bench_fwd(torch, E, Sd, x0, w, args.steps, args.warmup, flush)
     if args.only == "fwd":
@@ -539,6 +630,8 @@ def main():
                                  loads=Sc.cost_host()[0])
 
     e2e = bench_e2e(torch, S, x0, w)
+    e2e["value"] *= ws  # replicas: whole-job aggregate
+    e2e["resident_state"]["value"] *= ws
     tot = max_over_ranks(torch, sum(fwd["ms"]))
     value = ws * m * len(fwd["ms"]) / (1e-3 * tot)
     fb_tot = max_over_ranks(torch, sum(fb["ms"]))

@@ -46,6 +46,7 @@ extern "C" {
 /* ep_partition flags */
 #define EP_BIPARTITE 1u     /* SpMV graph: x_j -> vertex j, y_i -> vertex n+i */
 #define EP_DEFAULT_ORDER 2u /* no partitioning: C consecutive tasks per block */
+#define EP_PRESCREEN 4u     /* run ep_prescreen first and follow its verdict */
 
 /* kernels */
 #define EP_KERNEL_FLUX 0 /* f = w (x_v - x_u)/(1+|x_v - x_u|^2); out_u += f, out_v -= f */
@@ -72,7 +73,7 @@ const char *ep_last_error(void);
  *             x_{dst[e]} (vertex dst[e]) and y_{src[e]} (vertex n + src[e]).
  *   C         block capacity in tasks, 1 <= C <= EP_MAX_C; k = ceil(m/C)
  *             blocks, every block holds exactly C tasks except the last.
- *   flags     EP_BIPARTITE, EP_DEFAULT_ORDER.
+ *   flags     EP_BIPARTITE, EP_DEFAULT_ORDER, EP_PRESCREEN.
  *   threads   host threads for the recursion (<= 0: all hardware threads).
  *   out       receives a new schedule; free it with ep_schedule_free().
  * The result is deterministic and independent of `threads`.  Host-only: runs
@@ -115,6 +116,43 @@ int ep_job_wait(ep_job *job, int64_t timeout_ms, int32_t *done);
 int ep_job_take(ep_job *job, ep_schedule **out, double *seconds);
 int ep_job_cancel(ep_job *job);
 int ep_job_free(ep_job *job);
+
+/*
+ * Pre-screen (Section 4, the optimisation workflow): look at the graph before
+ * partitioning it.  Host-only.  Degrees count the tasks that use a data
+ * vertex (a self loop once).  The verdict, in this order:
+ *   EP_ORIGIN_PATH      the tasks form one simple path: preset schedule that
+ *                       walks the path from its smaller-id end and cuts it every
+ *                       C tasks; it loads m + k vertices, the optimum of Eq. 1
+ *                       (C path edges touch at least C + 1 vertices).
+ *   EP_ORIGIN_STAR      every task uses one centre and a leaf of its own: every
+ *                       schedule loads m + k, so the default order is kept.
+ *   EP_ORIGIN_LOW_REUSE mean degree of the touched vertices <= 2 (little
+ *                       data reuse): the default order is kept.
+ *   EP_ORIGIN_PARTITION otherwise: partition.
+ * The paper names the checks but neither their thresholds nor its preset
+ * schedules; these are this library's (the path and star presets are
+ * optimal, the reuse threshold is the paper's own remark that a mean degree
+ * of at most 2 leaves little sharing).  flags: EP_BIPARTITE only.
+ * ep_partition with EP_PRESCREEN applies the verdict; ep_schedule_origin()
+ * tells how a schedule's order was chosen (EP_ORIGIN_DEFAULT: asked for with
+ * EP_DEFAULT_ORDER).
+ */
+#define EP_ORIGIN_PARTITION 0
+#define EP_ORIGIN_DEFAULT 1
+#define EP_ORIGIN_PATH 2
+#define EP_ORIGIN_STAR 3
+#define EP_ORIGIN_LOW_REUSE 4
+typedef struct {
+  int64_t touched;    /* data vertices used by at least one task */
+  int64_t degree_sum; /* sum of their degrees */
+  int64_t max_degree;
+  int32_t origin;     /* the verdict, EP_ORIGIN_* */
+  int32_t pad;
+} ep_prescreen_info;
+int ep_prescreen(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, uint32_t flags,
+                 ep_prescreen_info *out);
+int ep_schedule_origin(const ep_schedule *s, int32_t *origin);
 
 /* Sizes of a schedule.  nd = number of data vertices (n, or 2n if bipartite).
  * Any output pointer may be NULL. */
@@ -274,6 +312,8 @@ int ep_set_threads(ep_schedule *s, int32_t threads);
  * the schedule block `ahead` positions later into L2; consumer warps
  * (ep_set_threads) gather foreign records with cp.async and compute one
  * stage while the next ones load.  Results agree up to FP32 rounding order.
+ * When two stages of the schedule's largest block do not fit in shared
+ * memory, launches use the stages = 0 kernel instead.
  */
 int ep_set_pipeline(ep_schedule *s, int32_t stages, int32_t ahead);
 
@@ -284,6 +324,23 @@ int ep_set_pipeline(ep_schedule *s, int32_t stages, int32_t ahead);
  * free stage).  *code = 0 and EP_OK when clean, else EP_ETIMEOUT.
  */
 int ep_check_errors(ep_schedule *s, int32_t *code, void *stream);
+
+/*
+ * Where the forward flux and SpMV kernels read a block's data from (the
+ * study of Section 5, Fig. 11 and Table 3: texture cache vs software cache).
+ * EP_CACHE_SMEM (default): staged into shared memory (the flux kernels
+ * chosen by ep_set_pipeline; SpMV stages x).  EP_CACHE_L1: nothing staged;
+ * every read goes through the read-only data cache (ld.global.nc, which
+ * replaces the texture binding of the paper's GPUs).  Flux: one CUDA block
+ * per schedule block, one thread per vertex position (up to 4 per thread).
+ * SpMV: x read through that cache, y written as before (EP-text of
+ * Section 5).  The adjoint keeps its staged kernels.  Results agree up to
+ * FP32 rounding order.  EP_EINVAL for another mode, or for EP_CACHE_L1 on a
+ * flux schedule whose block has more than 4096 vertex positions.
+ */
+#define EP_CACHE_SMEM 0
+#define EP_CACHE_L1 1
+int ep_set_cache(ep_schedule *s, int32_t mode);
 
 /*
  * Test hook for the bounded waits (no counterpart in the paper).  With

@@ -58,6 +58,8 @@ def _load():
             lib.orc_h_graph.restype = i32
             lib.orc_bisect.argtypes = [P, P, P, i32, i64, P]
             lib.orc_bisect.restype = i32
+            lib.orc_prescreen.argtypes = [P, P, i64, i64, u32, P, P]
+            lib.orc_prescreen.restype = i32
             lib.orc_partition.argtypes = [P, P, i64, i64, i32, u32, P]
             lib.orc_partition.restype = i32
             lib.orc_schedule.argtypes = [P, P, i64, i64, u32, P, i32, P, P, P, P, P, P]
@@ -106,11 +108,30 @@ def bisect(xadj, adj, ew, s_left: int) -> np.ndarray:
     return side
 
 
-def partition(src, dst, n: int, C: int, bipartite: bool = False, default_order: bool = False):
+PRESCREEN_VERDICTS = {0: "partition", 2: "path", 3: "star", 4: "low_reuse"}
+
+
+def prescreen(src, dst, n: int, bipartite: bool = False) -> dict:
+    """Pre-screen of Section 4's workflow (see orc_prescreen): degree summary,
+    verdict, and for a path the walk order of its tasks."""
+    src, dst = _edges(src, dst)
+    out = np.zeros(4, np.int64)
+    order = np.full(src.size, -1, np.int32)
+    if _load().orc_prescreen(_p(src), _p(dst), src.size, n, BIPARTITE if bipartite else 0,
+                             _p(out), _p(order)):
+        raise ValueError("orc_prescreen failed")
+    verdict = PRESCREEN_VERDICTS[int(out[3])]
+    return dict(touched=int(out[0]), degree_sum=int(out[1]), max_degree=int(out[2]),
+                origin=verdict, order=order if verdict == "path" else None)
+
+
+def partition(src, dst, n: int, C: int, bipartite: bool = False, default_order: bool = False,
+              prescreen: bool = False):
     """Block id of every task (edge); k = ceil(m / C) blocks."""
     src, dst = _edges(src, dst)
     part = np.zeros(src.size, np.int32)
-    flags = (BIPARTITE if bipartite else 0) | (DEFAULT_ORDER if default_order else 0)
+    flags = ((BIPARTITE if bipartite else 0) | (DEFAULT_ORDER if default_order else 0)
+             | (4 if prescreen else 0))
     rc = _load().orc_partition(_p(src), _p(dst), src.size, n, C, flags, _p(part))
     if rc:
         raise ValueError(f"orc_partition failed ({rc})")
@@ -140,9 +161,10 @@ def schedule(src, dst, n: int, part, bipartite: bool = False) -> dict:
                 loads=int(stats[0]), cut=int(stats[1]), touched=int(stats[2]))
 
 
-def ep_schedule(src, dst, n: int, C: int, bipartite: bool = False, default_order: bool = False):
+def ep_schedule(src, dst, n: int, C: int, bipartite: bool = False, default_order: bool = False,
+                prescreen: bool = False):
     """partition() followed by schedule(); adds 'part'."""
-    part = partition(src, dst, n, C, bipartite, default_order)
+    part = partition(src, dst, n, C, bipartite, default_order, prescreen)
     s = schedule(src, dst, n, part, bipartite)
     s["part"] = part
     return s

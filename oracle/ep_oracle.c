@@ -604,12 +604,99 @@ int32_t orc_bisect(const int64_t *xadj, const int32_t *adj, const int32_t *ew, i
   return 0;
 }
 
+/* Pre-screen before partitioning (Section 4, the optimisation workflow):
+ * out[0] = touched data vertices, out[1] = sum of their degrees (a self loop
+ * counts once), out[2] = max degree, out[3] = verdict: 2 path (one simple
+ * path: walk it from its smaller-id end), 3 star (one centre in every task,
+ * every other vertex a leaf), 4 low reuse (mean degree <= 2), 0 partition.
+ * The paper gives neither thresholds nor presets; these are the readings
+ * used here.  order[m] (may be NULL) receives the walk for a path. */
+int32_t orc_prescreen(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, uint32_t flags,
+                      int64_t *out, int32_t *order) {
+  if (check_edges(src, dst, m, n)) return -1;
+  int bip = (int)(flags & 1u);
+  int64_t nd = bip ? 2 * n : n;
+  int64_t *deg = calloc((size_t)nd, sizeof(int64_t));
+  int32_t *slot0 = malloc((size_t)nd * sizeof(int32_t)); /* first two incident tasks */
+  int32_t *slot1 = malloc((size_t)nd * sizeof(int32_t));
+  int loops = 0;
+  for (int64_t e = 0; e < m; e++) {
+    int64_t u, v;
+    endpoints(src, dst, e, n, bip, &u, &v);
+    int64_t ends[2] = {u, v};
+    int cnt = (u == v) ? 1 : 2;
+    if (u == v) loops = 1;
+    for (int i = 0; i < cnt; i++) {
+      int64_t x = ends[i];
+      if (deg[x] == 0) slot0[x] = (int32_t)e;
+      if (deg[x] == 1) slot1[x] = (int32_t)e;
+      deg[x]++;
+    }
+  }
+  int64_t touched = 0, sum = 0, maxd = 0, ones = 0, end0 = -1, centre = -1;
+  for (int64_t x = 0; x < nd; x++) {
+    if (deg[x] == 0) continue;
+    touched++;
+    sum += deg[x];
+    if (deg[x] > maxd) maxd = deg[x];
+    if (deg[x] == 1) {
+      ones++;
+      if (end0 < 0) end0 = x;
+    }
+    if (deg[x] == m && centre < 0) centre = x;
+  }
+  int64_t verdict = 0;
+  if (!loops && maxd <= 2 && ones == 2 && touched == m + 1) {
+    /* walk: leave each vertex by the incident task not arrived on */
+    int64_t x = end0, steps = 0;
+    int32_t prev = -1;
+    while (steps < m) {
+      int32_t e = -1;
+      if (slot0[x] != prev)
+        e = slot0[x];
+      else if (deg[x] == 2 && slot1[x] != prev)
+        e = slot1[x];
+      if (e < 0) break;
+      if (order) order[steps] = e;
+      steps++;
+      int64_t u, v;
+      endpoints(src, dst, e, n, bip, &u, &v);
+      x = (u == x) ? v : u;
+      prev = e;
+    }
+    if (steps == m) verdict = 2;
+  }
+  if (verdict == 0 && !loops && m >= 2 && centre >= 0 && touched == m + 1 && ones == m)
+    verdict = 3;
+  if (verdict == 0 && sum <= 2 * touched) verdict = 4;
+  out[0] = touched;
+  out[1] = sum;
+  out[2] = maxd;
+  out[3] = verdict;
+  free(deg);
+  free(slot0);
+  free(slot1);
+  return 0;
+}
+
 /* Edge partition: part[e] in [0, k), k = ceil(m / C).  flags bit 0 =
- * bipartite, bit 1 = default order (C consecutive tasks per block). */
+ * bipartite, bit 1 = default order (C consecutive tasks per block), bit 2 =
+ * pre-screen first (orc_prescreen): a path is cut every C tasks along its
+ * walk, a star or a low-reuse graph keeps the default order. */
 int32_t orc_partition(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, int32_t C,
                       uint32_t flags, int32_t *part) {
   if (C <= 0 || check_edges(src, dst, m, n)) return -1;
   int32_t k = (int32_t)((m + C - 1) / C);
+  if ((flags & 4u) && !(flags & 2u)) {
+    int64_t info[4];
+    int32_t *order = malloc((size_t)m * sizeof(int32_t));
+    orc_prescreen(src, dst, m, n, flags, info, order);
+    if (info[3] == 2)
+      for (int64_t i = 0; i < m; i++) part[order[i]] = (int32_t)(i / C);
+    free(order);
+    if (info[3] == 2) return 0;
+    if (info[3] == 3 || info[3] == 4) flags |= 2u;
+  }
   if ((flags & 2u) || k == 1) {
     for (int64_t e = 0; e < m; e++) part[e] = (int32_t)(e / C);
     return 0;

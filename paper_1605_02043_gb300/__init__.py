@@ -13,13 +13,17 @@ import numpy as np
 
 from ._lib import EpError, check, lib
 
-__all__ = ["Schedule", "PartitionJob", "EpError", "FLUX", "SPMV", "BIPARTITE", "DEFAULT_ORDER", "record_floats",
+__all__ = ["Schedule", "PartitionJob", "EpError", "prescreen", "FLUX", "SPMV", "BIPARTITE", "DEFAULT_ORDER", "record_floats",
            "T_EDGE_FWD", "T_BND", "T_EDGE_ADJ", "T_SPMV", "T_LAYOUT", "T_COST"]
 
 FLUX = 0
 SPMV = 1
 BIPARTITE = 1
 DEFAULT_ORDER = 2
+PRESCREEN = 4
+ORIGINS = ("partition", "default", "path", "star", "low_reuse")  # EP_ORIGIN_*
+CACHE_SMEM = 0  # ep_set_cache modes
+CACHE_L1 = 1
 JOB_TEST_FAIL = 0x100  # test hooks of ep_partition_start (host-side fault injection)
 JOB_TEST_HOLD = 0x200
 # kernel classes of Schedule.timing_read (EP_T_* in epcache.h)
@@ -60,6 +64,21 @@ def _edges(src, dst):
     return src, dst
 
 
+class _PrescreenInfo(ctypes.Structure):
+    _fields_ = [("touched", ctypes.c_int64), ("degree_sum", ctypes.c_int64),
+                ("max_degree", ctypes.c_int64), ("origin", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def prescreen(src, dst, n: int, bipartite: bool = False) -> dict:
+    """Verdict of the pre-screen (ep_prescreen): degree summary and origin name."""
+    src, dst = _edges(src, dst)
+    info = _PrescreenInfo()
+    check(lib().ep_prescreen(src.ctypes.data, dst.ctypes.data, src.size, n,
+                             BIPARTITE if bipartite else 0, ctypes.byref(info)))
+    return dict(touched=info.touched, degree_sum=info.degree_sum, max_degree=info.max_degree,
+                origin=ORIGINS[info.origin])
+
+
 def record_floats(D: int) -> int:
     return int(lib().ep_record_floats(D))
 
@@ -79,9 +98,11 @@ class Schedule:
     # ---------------------------------------------------------------- build
     @classmethod
     def partition(cls, src, dst, n: int, C: int, bipartite: bool = False,
-                  default_order: bool = False, threads: int = 0) -> "Schedule":
+                  default_order: bool = False, threads: int = 0,
+                  prescreen: bool = False) -> "Schedule":
         src, dst = _edges(src, dst)
-        flags = (BIPARTITE if bipartite else 0) | (DEFAULT_ORDER if default_order else 0)
+        flags = ((BIPARTITE if bipartite else 0) | (DEFAULT_ORDER if default_order else 0)
+                 | (PRESCREEN if prescreen else 0))
         h = ctypes.c_void_p()
         check(lib().ep_partition(src.ctypes.data, dst.ctypes.data, src.size, n, C, flags, threads,
                                  ctypes.byref(h)))
@@ -108,6 +129,13 @@ class Schedule:
     @property
     def bipartite(self) -> bool:
         return bool(self.flags & BIPARTITE)
+
+    @property
+    def origin(self) -> str:
+        """How the task order was chosen (ORIGINS)."""
+        o = ctypes.c_int32()
+        check(lib().ep_schedule_origin(self._h, ctypes.byref(o)))
+        return ORIGINS[o.value]
 
     # ---------------------------------------------------------------- views
     def arrays(self) -> dict:
@@ -197,6 +225,11 @@ class Schedule:
         check(lib().ep_check_errors(self._h, ctypes.byref(code), _stream(stream)))
         return code.value
 
+    def set_cache(self, mode: int):
+        """CACHE_SMEM (staged, default) or CACHE_L1 (read-only data cache, no staging)
+        for forward flux steps."""
+        check(lib().ep_set_cache(self._h, mode))
+
     def debug_stall(self, block_index: int):
         """Test hook: make the pipelined kernels' bounded waits expire (-1 turns it off)."""
         check(lib().ep_debug_stall(self._h, block_index))
@@ -259,9 +292,9 @@ class PartitionJob:
     """
 
     def __init__(self, src, dst, n: int, C: int, bipartite: bool = False, threads: int = 0,
-                 test: int = 0):
+                 prescreen: bool = False, test: int = 0):
         src, dst = _edges(src, dst)
-        flags = (BIPARTITE if bipartite else 0) | test
+        flags = (BIPARTITE if bipartite else 0) | (PRESCREEN if prescreen else 0) | test
         self._h = ctypes.c_void_p()
         check(lib().ep_partition_start(src.ctypes.data, dst.ctypes.data, src.size, n, C, flags,
                                        threads, ctypes.byref(self._h)))

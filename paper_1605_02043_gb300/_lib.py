@@ -27,6 +27,8 @@ SIGNATURES = {
     "ep_job_cancel": (ctypes.c_int, [P]),
     "ep_job_free": (ctypes.c_int, [P]),
     "ep_schedule_info": (ctypes.c_int, [P, P, P, P, P, P, P]),
+    "ep_prescreen": (ctypes.c_int, [P, P, I64, I64, U32, P]),
+    "ep_schedule_origin": (ctypes.c_int, [P, P]),
     "ep_schedule_arrays": (ctypes.c_int, [P, P, P, P, P, P]),
     "ep_cost_host": (ctypes.c_int, [P, P, P]),
     "ep_cost": (ctypes.c_int, [P, P, P, P]),
@@ -52,6 +54,7 @@ SIGNATURES = {
     "ep_set_pipeline": (ctypes.c_int, [P, I32, I32]),
     "ep_check_errors": (ctypes.c_int, [P, P, P]),
     "ep_debug_stall": (ctypes.c_int, [P, I32]),
+    "ep_set_cache": (ctypes.c_int, [P, I32]),
     "ep_schedule_free": (None, [P]),
     "ep_cost_noalloc": (ctypes.c_int, [P, P, P, I64, I64, I32, P, P]),
     "ep_noalloc_last_error": (ctypes.c_char_p, []),

@@ -146,6 +146,7 @@ struct ep_schedule {
   int stages = 3;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
   int ahead = 0;   // L2 prefetch distance of the pipelined kernels, in schedule blocks per CUDA block
   int stall = -1;  // test hook of the bounded waits (ep_debug_stall)
+  int cache = EP_CACHE_SMEM;  // forward flux kernel family (ep_set_cache)
   DBuf ws_ctl;     // [0] block counter, [1] error word
   int sm_count = 0;
   // launch plans of the pipelined kernels, cached per (D, adjoint) so that
@@ -285,8 +286,8 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
   L.stall = s->stall;
   optin -= 1024;  // room for the kernel's static shared memory
   while (L.stages > 2 && (int64_t)L.stages * L.stage_bytes > optin) --L.stages;
-  if ((int64_t)L.stages * L.stage_bytes > optin)
-    return fail(EP_EINVAL, "a schedule block needs %d bytes of shared memory (limit %d)", L.stage_bytes, optin);
+  P.fits = (int64_t)L.stages * L.stage_bytes <= optin;
+  if (!P.fits) return EP_OK;  // the launch falls back to one CUDA block per schedule block
   P.smem = (size_t)L.stages * L.stage_bytes;
   P.threads = 32 * (L.ahead > 0 ? 2 : 1) + s->tpb;  // producer (+ prefetch) warp, consumer warps
   const void* kern = ep::dev::flux_tma_kernel_ptr(D, adjoint);
@@ -328,12 +329,20 @@ int ensure_bacc(ep_schedule* s, int32_t R, cudaStream_t st) {
 int flux_step_any(ep_schedule* s, int32_t D, const float* w, const float* x_in, float* x_out,
                   float* out, float tau, cudaStream_t st) {
   ep::dev::FluxArgs a = flux_args(s, w, x_in, x_out, out, tau);
+  if (s->cache == EP_CACHE_L1) {
+    CU(ep::dev::flux_step_ldg(a, D, st));
+    return EP_OK;
+  }
   if (s->stages == 0) {
     CU(ep::dev::flux_step(a, D, st));
     return EP_OK;
   }
   ep::dev::TmaPlan P;
   if (int rc = tma_plan(s, D, false, P)) return rc;
+  if (!P.fits) {
+    CU(ep::dev::flux_step(a, D, st));
+    return EP_OK;
+  }
   if (a.k > 0) {
     struct Scope {
       ep::dev::Timer* t;
@@ -361,6 +370,10 @@ int flux_adj_any(ep_schedule* s, int32_t D, const float* w, const float* x, floa
   }
   ep::dev::TmaPlan P;
   if (int rc = tma_plan(s, D, true, P)) return rc;
+  if (!P.fits) {
+    CU(ep::dev::flux_adjoint_step(a, D, lam, gw, st));
+    return EP_OK;
+  }
   if (a.k > 0) {
     struct Scope {
       ep::dev::Timer* t;
@@ -406,6 +419,7 @@ int spmv_lay(ep_schedule* s, const float* x_lay, const float* w_lay, float* y_la
   a.max_ny = h.max_ny;
   a.max_ne = h.max_ne;
   a.tpb = s->tpb;
+  a.readonly = s->cache == EP_CACHE_L1;
   a.timer = s->t();
   CU(ep::dev::spmv(a, st));
   return EP_OK;
@@ -438,7 +452,8 @@ int check_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, in
   if (m <= 0 || m >= INT32_MAX) return fail(EP_EINVAL, "m = %lld out of range", (long long)m);
   if (n <= 0 || n >= INT32_MAX / 2) return fail(EP_EINVAL, "n = %lld out of range", (long long)n);
   if (C < 1 || C > EP_MAX_C) return fail(EP_EINVAL, "C = %d out of [1, %d]", C, EP_MAX_C);
-  if (flags & ~(EP_BIPARTITE | EP_DEFAULT_ORDER)) return fail(EP_EINVAL, "unknown flags");
+  if (flags & ~(EP_BIPARTITE | EP_DEFAULT_ORDER | EP_PRESCREEN))
+    return fail(EP_EINVAL, "unknown flags");
   for (int64_t e = 0; e < m; ++e)
     if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
       return fail(EP_EINVAL, "task %lld uses a vertex outside [0, %lld)", (long long)e, (long long)n);
@@ -455,12 +470,25 @@ int fill_partition(ep_schedule* s, const int32_t* src, const int32_t* dst, int64
     h.n = n;
     h.nd = (flags & EP_BIPARTITE) ? 2 * n : n;
     h.C = C;
-    h.flags = flags;
+    h.flags = flags & ~EP_PRESCREEN;
     h.k = (m + C - 1) / C;
     h.src.assign(src, src + m);
     h.dst.assign(dst, dst + m);
     h.part.resize(m);
-    if (!ep::partition_edges(src, dst, m, n, C, flags, threads, h.part.data(), stop))
+    h.origin = (flags & EP_DEFAULT_ORDER) ? ep::kOriginDefault : ep::kOriginPartition;
+    bool placed = false;
+    if ((flags & EP_PRESCREEN) && !(flags & EP_DEFAULT_ORDER)) {
+      const ep::PrescreenResult pr = ep::prescreen(src, dst, m, n, (flags & EP_BIPARTITE) != 0);
+      h.origin = pr.origin;
+      if (pr.origin == ep::kOriginPath) {
+        for (int64_t i = 0; i < m; ++i) h.part[pr.order[i]] = (int32_t)(i / C);
+        placed = true;
+      } else if (pr.origin != ep::kOriginPartition) {
+        for (int64_t e = 0; e < m; ++e) h.part[e] = (int32_t)(e / C);
+        placed = true;
+      }
+    }
+    if (!placed && !ep::partition_edges(src, dst, m, n, C, h.flags, threads, h.part.data(), stop))
       return fail(EP_ECANCELED, "partition cancelled");
     if (stop && stop->load()) return fail(EP_ECANCELED, "partition cancelled");
     std::string err = ep::build_schedule(h, threads);
@@ -492,7 +520,8 @@ struct ep_job {
 
 namespace {
 
-constexpr int kHoldSeconds = 60;  // a held test job gives up after this long
+constexpr int kHoldSeconds = 60;        // a held test job gives up after this long
+constexpr int kLdgMaxPositions = 4096;  // 4 positions per thread, 1024 threads
 
 void job_main(ep_job* j) {
   const auto t0 = std::chrono::steady_clock::now();
@@ -623,6 +652,31 @@ int ep_job_free(ep_job* j) {
   if (j->th.joinable()) j->th.join();
   delete j->result;
   delete j;
+  return EP_OK;
+}
+
+int ep_prescreen(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, uint32_t flags,
+                 ep_prescreen_info* out) {
+  g_error.clear();
+  if (!out) return fail(EP_EINVAL, "null output pointer");
+  if (flags & ~EP_BIPARTITE) return fail(EP_EINVAL, "unknown flags");
+  if (int rc = check_edges(src, dst, m, n, 1, flags)) return rc;
+  try {
+    const ep::PrescreenResult pr = ep::prescreen(src, dst, m, n, (flags & EP_BIPARTITE) != 0);
+    out->touched = pr.touched;
+    out->degree_sum = pr.degree_sum;
+    out->max_degree = pr.max_degree;
+    out->origin = pr.origin;
+  } catch (const std::bad_alloc&) {
+    return fail(EP_ENOMEM, "out of host memory");
+  }
+  return EP_OK;
+}
+
+int ep_schedule_origin(const ep_schedule* s, int32_t* origin) {
+  g_error.clear();
+  if (!s || !origin) return fail(EP_EINVAL, "null argument");
+  *origin = s->h.origin;
   return EP_OK;
 }
 
@@ -993,6 +1047,16 @@ int ep_check_errors(ep_schedule* s, int32_t* code, void* stream) {
     s->bacc_dirty = true;  // an interrupted launch may have left partial sums
     return fail(EP_ETIMEOUT, "a pipelined kernel gave up waiting (code %d)", v[1]);
   }
+  return EP_OK;
+}
+
+int ep_set_cache(ep_schedule* s, int32_t mode) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (mode != EP_CACHE_SMEM && mode != EP_CACHE_L1) return fail(EP_EINVAL, "cache mode %d", mode);
+  if (mode == EP_CACHE_L1 && !bipartite(s) && s->h.max_nv > kLdgMaxPositions)
+    return fail(EP_EINVAL, "a block has %d positions; the read-only-cache kernel takes at most %d",
+                s->h.max_nv, kLdgMaxPositions);
+  s->cache = mode;
   return EP_OK;
 }
 

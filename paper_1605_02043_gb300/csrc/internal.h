@@ -60,6 +60,7 @@ struct HostSchedule {
   int64_t m = 0, n = 0, nd = 0, k = 0;
   int32_t C = 0;
   uint32_t flags = 0;
+  int32_t origin = 0;             // how the task order was chosen (kOrigin*)
   std::vector<int32_t> src, dst;  // caller's task list
   std::vector<int32_t> part;      // block of every task
   std::vector<int64_t> block_ptr, vert_ptr;
@@ -94,8 +95,19 @@ struct HostSchedule {
   std::vector<uint32_t> loc;  // per task in edge_perm order: slot(u) | slot(v) << 16
 };
 
-// partition.cpp
-// Returns false (part unfinished) when *stop became non-zero during the run.
+// prescreen.cpp: checks made before partitioning (Section 4 workflow).
+// Origins match EP_ORIGIN_* in epcache.h.
+constexpr int32_t kOriginPartition = 0, kOriginDefault = 1, kOriginPath = 2, kOriginStar = 3,
+                  kOriginLowReuse = 4;
+struct PrescreenResult {
+  int64_t touched = 0, degree_sum = 0, max_degree = 0;
+  int32_t origin = kOriginPartition;
+  std::vector<int32_t> order;  // path preset: the tasks in walk order
+};
+PrescreenResult prescreen(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, bool bip);
+
+// partition.cpp.  Returns false (part unfinished) when *stop became non-zero
+// during the run.
 bool partition_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t n, int32_t C,
                      uint32_t flags, int threads, int32_t* part,
                      const std::atomic<int>* stop = nullptr);

@@ -230,6 +230,66 @@ __global__ void __launch_bounds__(1024) flux_fwd_kernel(
   }
 }
 
+// Read-only-cache variant: the texture-cache kernel of Section 5 (Fig. 7(c)),
+// with the read-only data cache (ld.global.nc) in place of texture binding.
+// No staging: every read of a block's incidence, weights and states goes to
+// global memory through that cache.  Thread t handles positions t, t + T,
+// ..., t + (R-1) T of its block and keeps their sums in registers; writes
+// wait for a block barrier, because interior records are updated in place
+// and other threads of the same block may still be reading them.  Foreign
+// and boundary records are never written by this kernel.
+template <int D, int R>
+__global__ void __launch_bounds__(1024) flux_fwd_ldg_kernel(
+    const FluxDesc* __restrict__ desc, const int32_t* __restrict__ flist,
+    const uint32_t* __restrict__ inc, const uint16_t* __restrict__ ptr, const float* __restrict__ w,
+    const float* x_in, float* x_out, float* __restrict__ bacc, float* __restrict__ out,
+    int64_t n_rec, int64_t n_int, int64_t n_bnd, float tau) {
+  const FluxDesc d = desc[blockIdx.x];
+  float xp[R][D], acc[R][D];
+  int32_t rec[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int p = (int)threadIdx.x + i * (int)blockDim.x;
+    rec[i] = -1;
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[i][c] = 0.f;
+    if (p >= d.np) continue;
+    const int k0 = __ldg(ptr + d.q0 + p), k1 = __ldg(ptr + d.q0 + p + 1);
+    if (k0 == k1) continue;  // unused position
+    rec[i] = flux_rec(d, flist, p);
+    rec_load<D, true>(x_in, n_rec, rec[i], xp[i]);
+    for (int k = k0; k < k1; ++k) {
+      const uint32_t e = __ldg(inc + d.i0 + k);
+      float xo[D];
+      rec_load<D, true>(x_in, n_rec, flux_rec(d, flist, (int)(e & kPosMask)), xo);
+      float dd[D], q = 0.f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        dd[c] = xo[c] - xp[i][c];
+        q = fmaf(dd[c], dd[c], q);
+      }
+      const float coef = __fdividef(__ldg(w + d.w0 + ((e >> kTaskShift) & 0xffffu)), 1.f + q);
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[i][c] = fmaf(coef, dd[c], acc[i][c]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int p = (int)threadIdx.x + i * (int)blockDim.x;
+    if (rec[i] < 0) continue;
+    if (p < d.pi + d.n_int) {
+      float xn[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) xn[c] = fmaf(tau, acc[i][c], xp[i][c]);
+      rec_store<D>(x_out, n_rec, rec[i], xn);
+      if (out) rec_store<D>(out, n_rec, rec[i], acc[i]);
+    } else {
+      rec_red<D>(bacc, n_bnd, rec[i] - n_int, acc[i]);
+    }
+  }
+}
+
 // shared records: x_out = x_in + tau * acc; out = acc; acc = 0 (plane by plane)
 template <int D>
 __global__ void bnd_update_kernel(const float* x_in, float* x_out, float* __restrict__ bacc,
@@ -541,6 +601,36 @@ cudaError_t flux_step_t(const FluxArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int D, int R>
+void flux_ldg_launch(const FluxArgs& a, int threads, cudaStream_t st) {
+  flux_fwd_ldg_kernel<D, R><<<(unsigned)a.k, threads, 0, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w,
+                                                              a.x_in, a.x_out, a.bacc, a.out,
+                                                              a.n_rec, a.n_int, a.n_bnd, a.tau);
+}
+
+template <int D>
+cudaError_t flux_step_ldg_t(const FluxArgs& a, cudaStream_t st) {
+  const int R = (a.max_np + 1023) / 1024;  // positions per thread
+  const int threads = std::max(32, (((a.max_np + R - 1) / R) + 31) / 32 * 32);
+  if (a.k > 0) {
+    Scope sc(a.timer, T_EDGE_FWD, st);
+    switch (R) {
+      case 0:
+      case 1: flux_ldg_launch<D, 1>(a, threads, st); break;
+      case 2: flux_ldg_launch<D, 2>(a, threads, st); break;
+      case 3: flux_ldg_launch<D, 3>(a, threads, st); break;
+      case 4: flux_ldg_launch<D, 4>(a, threads, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (a.n_bnd > 0) {
+    Scope sc(a.timer, T_BND, st);
+    bnd_update_kernel<D><<<grid_for(a.n_bnd, 256), 256, 0, st>>>(a.x_in, a.x_out, a.bacc, a.out,
+                                                                 a.n_rec, a.n_int, a.n_bnd, a.tau);
+  }
+  return cudaGetLastError();
+}
+
 template <int D>
 cudaError_t flux_adj_t(const FluxArgs& a, float* lam, float* gw, cudaStream_t st) {
   const size_t smem = flux_smem_bytes(a, D, 2);
@@ -572,6 +662,20 @@ cudaError_t flux_step(const FluxArgs& a, int D, cudaStream_t st) {
     case 6: return flux_step_t<6>(a, st);
     case 7: return flux_step_t<7>(a, st);
     case 8: return flux_step_t<8>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t flux_step_ldg(const FluxArgs& a, int D, cudaStream_t st) {
+  switch (D) {
+    case 1: return flux_step_ldg_t<1>(a, st);
+    case 2: return flux_step_ldg_t<2>(a, st);
+    case 3: return flux_step_ldg_t<3>(a, st);
+    case 4: return flux_step_ldg_t<4>(a, st);
+    case 5: return flux_step_ldg_t<5>(a, st);
+    case 6: return flux_step_ldg_t<6>(a, st);
+    case 7: return flux_step_ldg_t<7>(a, st);
+    case 8: return flux_step_ldg_t<8>(a, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -616,6 +720,47 @@ cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, c
   return cudaErrorInvalidValue;
 }
 
+// Read-only-cache SpMV (EP-text of Section 5): the same row-pull form with
+// nothing staged; x, the task weights, entries and offsets are read through
+// the read-only data cache.  y is written as in spmv_kernel.
+__global__ void __launch_bounds__(1024) spmv_ldg_kernel(
+    const SpmvDesc* __restrict__ desc, const int32_t* __restrict__ xlist,
+    const int32_t* __restrict__ ylist, const uint32_t* __restrict__ inc,
+    const uint16_t* __restrict__ ptr, const float* __restrict__ w, const float* __restrict__ x,
+    float* __restrict__ y) {
+  const SpmvDesc d = desc[blockIdx.x];
+  const int ny = d.n_yi + d.n_yob + d.n_yf;
+  const uint32_t* es = inc + d.i0;
+  const uint16_t* ps = ptr + d.q0;
+  const float* ws = w + d.w0;
+  auto xval = [&](uint32_t e) {
+    const int i = (int)(e & kPosMask);
+    return __ldg(x + (i < d.n_xo ? d.x_lo + i : __ldg(xlist + d.fx0 + (i - d.n_xo))));
+  };
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int p = warp; p < ny; p += nw) {
+    const int k0 = __ldg(ps + p), k1 = __ldg(ps + p + 1);
+    if (k1 - k0 <= 32) continue;  // warp-uniform
+    float acc = 0.f;
+    for (int q = k0 + lane; q < k1; q += 32) {
+      const uint32_t e = __ldg(es + q);
+      acc = fmaf(__ldg(ws + (e >> kTaskShift)), xval(e), acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) spmv_write(d, ylist, y, p, acc);
+  }
+  for (int p = threadIdx.x; p < ny; p += blockDim.x) {
+    const int k0 = __ldg(ps + p), k1 = __ldg(ps + p + 1);
+    if (k1 - k0 > 32 || k1 == k0) continue;
+    float acc = 0.f;
+    for (int q = k0; q < k1; ++q) {
+      const uint32_t e = __ldg(es + q);
+      acc = fmaf(__ldg(ws + (e >> kTaskShift)), xval(e), acc);
+    }
+    spmv_write(d, ylist, y, p, acc);
+  }
+}
+
 cudaError_t spmv(const SpmvArgs& a, cudaStream_t st) {
   const size_t smem = (size_t)(a.max_nx + 4) * sizeof(float) + (size_t)(a.max_ne + 4) * 8 +
                       (size_t)(a.max_ny + 1) * sizeof(uint16_t) + 16;
@@ -627,7 +772,12 @@ cudaError_t spmv(const SpmvArgs& a, cudaStream_t st) {
   }
   if (a.k > 0) {
     Scope sc(a.timer, T_SPMV, st);
-    spmv_kernel<<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.xlist, a.ylist, a.inc, a.ptr, a.w, a.x, a.y);
+    if (a.readonly)
+      spmv_ldg_kernel<<<(unsigned)a.k, a.tpb, 0, st>>>(a.desc, a.xlist, a.ylist, a.inc, a.ptr, a.w,
+                                                       a.x, a.y);
+    else
+      spmv_kernel<<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.xlist, a.ylist, a.inc, a.ptr, a.w,
+                                                      a.x, a.y);
   }
   return cudaGetLastError();
 }

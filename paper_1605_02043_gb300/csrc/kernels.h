@@ -49,6 +49,7 @@ struct SpmvArgs {
   int64_t ny_int, ny_zero;
   int32_t max_nx, max_ny, max_ne;
   int tpb;
+  bool readonly = false;  // spmv_ldg_kernel: nothing staged
   Timer* timer;
 };
 
@@ -80,6 +81,7 @@ struct TmaPlan {
   int grid, threads;
   size_t smem;
   int* err;  // error word (bit 0: a "full" wait expired, bit 1: an "empty" wait expired)
+  bool fits = true;  // false: two stages exceed shared memory; use the one-block kernel
 };
 cudaError_t flux_fwd_tma(const FluxArgs& a, const TmaPlan& P, int D, cudaStream_t st);
 cudaError_t flux_adj_tma(const FluxArgs& a, const TmaPlan& P, int D, float* lam, float* gw,
@@ -87,6 +89,8 @@ cudaError_t flux_adj_tma(const FluxArgs& a, const TmaPlan& P, int D, float* lam,
 const void* flux_tma_kernel_ptr(int D, bool adjoint);
 
 cudaError_t flux_step(const FluxArgs& a, int D, cudaStream_t st);
+// read-only-cache variant (no staging); needs max_np <= 4096
+cudaError_t flux_step_ldg(const FluxArgs& a, int D, cudaStream_t st);
 cudaError_t bnd_update(const FluxArgs& a, int D, float* x_in_out, const float* x_in, float* out,
                        cudaStream_t st);
 cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st);

@@ -81,6 +81,32 @@ def test_flux_state_widths(small_mesh, D, stages):
     assert rel_l2(x.cpu().numpy(), xT) <= RTOL
 
 
+@pytest.mark.parametrize("C,default_order", [(256, False), (64, False), (1000, False),
+                                              (256, True), (1000, True), (2000, True)])
+@pytest.mark.parametrize("D", [1, 5, 8])
+def test_flux_read_only_cache_variant(small_mesh, C, default_order, D):
+    # 1000 and 2000 tasks in default order give blocks of 2 to 4 positions per thread
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, C, default_order=default_order)
+    S.set_cache(E.CACHE_L1)
+    x0 = W.flux_state(n, D, 4)
+    w = W.flux_weights(src.size, 4)
+    x = cuda(x0)
+    out = torch.zeros_like(x)
+    S.run(x, cuda(w), out, steps=3, tau=1e-2)
+    xT, fT = O.flux_steps(src, dst, x0, w, 3, 1e-2)
+    assert rel_l2(out.cpu().numpy(), fT) <= RTOL
+    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
+    # the adjoint keeps its staged kernel under this mode
+    g = W.loss_weights(n, D, 1)
+    lam = cuda(g)
+    gw = torch.zeros(src.size, device="cuda")
+    S.run_adjoint(cuda(x0), cuda(w), lam, gw, steps=2, tau=1e-2)
+    dx, dw = O.flux_adjoint(src, dst, x0, w, 2, 1e-2, g)
+    assert rel_l2(lam.cpu().numpy(), dx) <= RTOL
+    assert rel_l2(gw.cpu().numpy(), dw) <= RTOL
+
+
 def test_flux_tau_zero_is_pure_flux(small_mesh):
     src, dst, n = small_mesh
     S = E.Schedule.partition(src, dst, n, 128)
@@ -152,6 +178,18 @@ def test_step_api_matches_run(small_mesh):
     xT, fT = O.flux_steps(src, dst, x0, w, 2, 1e-3)
     assert rel_l2(x.cpu().numpy(), xT) <= RTOL
     assert rel_l2(out.cpu().numpy(), fT) <= RTOL
+
+
+@pytest.mark.parametrize("C,default_order", [(512, False), (512, True), (64, False), (2048, True)])
+def test_spmv_read_only_cache(C, default_order):
+    n = 1 << 12
+    r, c = W.rmat(scale=12, m_draws=1 << 16, seed=1)
+    x0, w = W.spmv_inputs(n, r.size, 0)
+    S = E.Schedule.partition(r, c, n, C, bipartite=True, default_order=default_order)
+    S.set_cache(E.CACHE_L1)
+    y = torch.full((n,), 3.0, device="cuda")
+    S.run(cuda(x0), cuda(w), y, kernel=E.SPMV)
+    assert rel_l2(y.cpu().numpy(), O.spmv(r, c, x0, w, n)) <= RTOL
 
 
 @pytest.mark.parametrize("C,default_order,threads", [(512, False, 192), (512, True, 192), (64, False, 64),

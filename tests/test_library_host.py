@@ -127,6 +127,17 @@ def test_invalid_arguments():
         assert ei.value.code == -1
     S.debug_stall(0)
     S.debug_stall(-1)
+    for bad in (-1, 2):
+        with pytest.raises(E.EpError):
+            S.set_cache(bad)
+    S.set_cache(E.CACHE_L1)
+    S.set_cache(E.CACHE_SMEM)
+    # blocks of more than 4096 vertex positions are too large for the L1 variant
+    s2, d2 = W.knn_mesh(20000, 4, 0)
+    big = E.Schedule.partition(s2, d2, 20000, 4000, default_order=True)
+    with pytest.raises(E.EpError) as ei:
+        big.set_cache(E.CACHE_L1)
+    assert ei.value.code == -1 and "4096" in str(ei.value)
 
 
 def test_kernel_calls_need_a_device():
