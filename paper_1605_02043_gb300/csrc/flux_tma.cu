@@ -534,7 +534,8 @@ __global__ void __launch_bounds__(1024) flux_adj_tma_kernel(
         const float two = 2.f * dg * inv * inv;
 #pragma unroll
         for (int c = 0; c < D; ++c) acc[c] -= we * (g[c] * inv - two * dd[c]);
-        if (e & kSrcBit) gw[d.w0 + t] += tau * dg * inv;
+        // one writer per task: a fire-and-forget reduction instead of a load in the loop
+        if (e & kSrcBit) atomicAdd(gw + d.w0 + t, tau * dg * inv);
       }
       const int32_t r = pos_rec(d, S.flist, p);
       if (p < d.pi + d.n_int) {

@@ -354,7 +354,8 @@ __global__ void __launch_bounds__(1024) flux_adj_kernel(
       const float two = 2.f * dg * inv * inv;
 #pragma unroll
       for (int c = 0; c < D; ++c) acc[c] -= we * (g[c] * inv - two * dd[c]);
-      if (e & kSrcBit) gw[d.w0 + t] += tau * dg * inv;
+      // one writer per task: a fire-and-forget reduction instead of a load in the loop
+      if (e & kSrcBit) atomicAdd(gw + d.w0 + t, tau * dg * inv);
     }
     const int32_t r = flux_rec(d, flist, p);
     if (p < d.pi + d.n_int) {
@@ -401,8 +402,21 @@ __global__ void __launch_bounds__(1024) spmv_kernel(
     es[i] = __ldg(inc + d.i0 + i);
   }
   for (int i = threadIdx.x; i <= ny; i += blockDim.x) ps[i] = __ldg(ptr + d.q0 + i);
-  for (int i = threadIdx.x; i < nx; i += blockDim.x)
-    xs[i] = __ldg(x + (i < d.n_xo ? d.x_lo + i : __ldg(xlist + d.fx0 + (i - d.n_xo))));
+  // x entries: four (id, value) load chains in flight per thread
+  for (int i0 = threadIdx.x; i0 < nx; i0 += 4 * blockDim.x) {
+    int32_t r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      r[u] = i >= nx ? -1 : (i < d.n_xo ? d.x_lo + i : __ldg(xlist + d.fx0 + (i - d.n_xo)));
+    }
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = r[u] >= 0 ? __ldg(x + r[u]) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (r[u] >= 0) xs[i0 + u * (int)blockDim.x] = v[u];
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int p = warp; p < ny; p += nw) {
