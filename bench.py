@@ -174,8 +174,10 @@ def barrier(torch):
 
 
 def max_over_ranks(torch, value):
+    """Max of a host number over all ranks (NCCL on GPUs, gloo in CPU tests)."""
     if torch.distributed.is_available() and torch.distributed.is_initialized():
-        t = torch.tensor([value], dtype=torch.float64, device="cuda")
+        dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
     return value
