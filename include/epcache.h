@@ -46,7 +46,7 @@ extern "C" {
 /* ep_partition flags */
 #define EP_BIPARTITE 1u     /* SpMV graph: x_j -> vertex j, y_i -> vertex n+i */
 #define EP_DEFAULT_ORDER 2u /* no partitioning: C consecutive tasks per block */
-#define EP_PRESCREEN 4u     /* run ep_prescreen first and follow its verdict */
+#define EP_PRESCREEN 4u     /* run ep_prescreen first and follow its outcome */
 
 /* kernels */
 #define EP_KERNEL_FLUX 0 /* f = w (x_v - x_u)/(1+|x_v - x_u|^2); out_u += f, out_v -= f */
@@ -120,7 +120,7 @@ int ep_job_free(ep_job *job);
 /*
  * Pre-screen (Section 4, the optimisation workflow): look at the graph before
  * partitioning it.  Host-only.  Degrees count the tasks that use a data
- * vertex (a self loop once).  The verdict, in this order:
+ * vertex (a self loop once).  The outcome, in this order:
  *   EP_ORIGIN_PATH      the tasks form one simple path: preset schedule that
  *                       walks the path from its smaller-id end and cuts it every
  *                       C tasks; it loads m + k vertices, the optimum of Eq. 1
@@ -134,7 +134,7 @@ int ep_job_free(ep_job *job);
  * schedules; these are this library's (the path and star presets are
  * optimal, the reuse threshold is the paper's own remark that a mean degree
  * of at most 2 leaves little sharing).  flags: EP_BIPARTITE only.
- * ep_partition with EP_PRESCREEN applies the verdict; ep_schedule_origin()
+ * ep_partition with EP_PRESCREEN applies the outcome; ep_schedule_origin()
  * tells how a schedule's order was chosen (EP_ORIGIN_DEFAULT: asked for with
  * EP_DEFAULT_ORDER).
  */
@@ -147,7 +147,7 @@ typedef struct {
   int64_t touched;    /* data vertices used by at least one task */
   int64_t degree_sum; /* sum of their degrees */
   int64_t max_degree;
-  int32_t origin;     /* the verdict, EP_ORIGIN_* */
+  int32_t origin;     /* the outcome, EP_ORIGIN_* */
   int32_t pad;
 } ep_prescreen_info;
 int ep_prescreen(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, uint32_t flags,

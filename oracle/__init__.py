@@ -108,21 +108,21 @@ def bisect(xadj, adj, ew, s_left: int) -> np.ndarray:
     return side
 
 
-PRESCREEN_VERDICTS = {0: "partition", 2: "path", 3: "star", 4: "low_reuse"}
+PRESCREEN_OUTCOMES = {0: "partition", 2: "path", 3: "star", 4: "low_reuse"}
 
 
 def prescreen(src, dst, n: int, bipartite: bool = False) -> dict:
     """Pre-screen of Section 4's workflow (see orc_prescreen): degree summary,
-    verdict, and for a path the walk order of its tasks."""
+    outcome, and for a path the walk order of its tasks."""
     src, dst = _edges(src, dst)
     out = np.zeros(4, np.int64)
     order = np.full(src.size, -1, np.int32)
     if _load().orc_prescreen(_p(src), _p(dst), src.size, n, BIPARTITE if bipartite else 0,
                              _p(out), _p(order)):
         raise ValueError("orc_prescreen failed")
-    verdict = PRESCREEN_VERDICTS[int(out[3])]
+    outcome = PRESCREEN_OUTCOMES[int(out[3])]
     return dict(touched=int(out[0]), degree_sum=int(out[1]), max_degree=int(out[2]),
-                origin=verdict, order=order if verdict == "path" else None)
+                origin=outcome, order=order if outcome == "path" else None)
 
 
 def partition(src, dst, n: int, C: int, bipartite: bool = False, default_order: bool = False,

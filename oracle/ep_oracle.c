@@ -606,7 +606,7 @@ int32_t orc_bisect(const int64_t *xadj, const int32_t *adj, const int32_t *ew, i
 
 /* Pre-screen before partitioning (Section 4, the optimisation workflow):
  * out[0] = touched data vertices, out[1] = sum of their degrees (a self loop
- * counts once), out[2] = max degree, out[3] = verdict: 2 path (one simple
+ * counts once), out[2] = max degree, out[3] = outcome: 2 path (one simple
  * path: walk it from its smaller-id end), 3 star (one centre in every task,
  * every other vertex a leaf), 4 low reuse (mean degree <= 2), 0 partition.
  * The paper gives neither thresholds nor presets; these are the readings
@@ -645,7 +645,7 @@ int32_t orc_prescreen(const int32_t *src, const int32_t *dst, int64_t m, int64_t
     }
     if (deg[x] == m && centre < 0) centre = x;
   }
-  int64_t verdict = 0;
+  int64_t outcome = 0;
   if (!loops && maxd <= 2 && ones == 2 && touched == m + 1) {
     /* walk: leave each vertex by the incident task not arrived on */
     int64_t x = end0, steps = 0;
@@ -664,15 +664,15 @@ int32_t orc_prescreen(const int32_t *src, const int32_t *dst, int64_t m, int64_t
       x = (u == x) ? v : u;
       prev = e;
     }
-    if (steps == m) verdict = 2;
+    if (steps == m) outcome = 2;
   }
-  if (verdict == 0 && !loops && m >= 2 && centre >= 0 && touched == m + 1 && ones == m)
-    verdict = 3;
-  if (verdict == 0 && sum <= 2 * touched) verdict = 4;
+  if (outcome == 0 && !loops && m >= 2 && centre >= 0 && touched == m + 1 && ones == m)
+    outcome = 3;
+  if (outcome == 0 && sum <= 2 * touched) outcome = 4;
   out[0] = touched;
   out[1] = sum;
   out[2] = maxd;
-  out[3] = verdict;
+  out[3] = outcome;
   free(deg);
   free(slot0);
   free(slot1);

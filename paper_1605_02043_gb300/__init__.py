@@ -70,7 +70,7 @@ class _PrescreenInfo(ctypes.Structure):
 
 
 def prescreen(src, dst, n: int, bipartite: bool = False) -> dict:
-    """Verdict of the pre-screen (ep_prescreen): degree summary and origin name."""
+    """Outcome of the pre-screen (ep_prescreen): degree summary and origin name."""
     src, dst = _edges(src, dst)
     info = _PrescreenInfo()
     check(lib().ep_prescreen(src.ctypes.data, dst.ctypes.data, src.size, n,

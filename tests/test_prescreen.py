@@ -1,5 +1,5 @@
 """Pre-screen before partitioning (Section 4, the optimisation workflow): the
-oracle's verdicts and presets pinned to closed forms and brute force, and the
+oracle's outcomes and presets pinned to closed forms and brute force, and the
 library's pre-screen bit-exact with the oracle.  No GPU needed."""
 import numpy as np
 import pytest
