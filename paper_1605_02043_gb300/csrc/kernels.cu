@@ -150,8 +150,8 @@ __device__ __forceinline__ FluxSmem flux_smem(const FluxDesc& d, bool with_lam) 
   s.x = reinterpret_cast<float*>(smem4);
   s.lam = s.x + D * s.npos;
   s.w = with_lam ? s.lam + D * s.npos : s.lam;
-  s.ent = reinterpret_cast<uint32_t*>(s.w + d.ne);
-  s.ptr = reinterpret_cast<uint16_t*>(s.ent + d.nent);
+  s.ent = reinterpret_cast<uint32_t*>(s.w + ((d.ne + 3) & ~3));  // 16-byte aligned pieces
+  s.ptr = reinterpret_cast<uint16_t*>(s.ent + ((d.nent + 3) & ~3));
   return s;
 }
 
@@ -162,10 +162,16 @@ __device__ __forceinline__ void stage_block(const FluxDesc& d, const FluxSmem& s
                                             const uint16_t* __restrict__ ptr,
                                             const float* __restrict__ w, const float* x, int64_t n_rec,
                                             const float* lam) {
-  // independent loads first, so no warp waits on a foreign id before issuing them
-  for (int i = threadIdx.x; i < d.ne; i += blockDim.x) s.w[i] = __ldg(w + d.w0 + i);
-  for (int i = threadIdx.x; i < d.nent; i += blockDim.x) s.ent[i] = __ldg(inc + d.i0 + i);
-  for (int i = threadIdx.x; i <= d.np; i += blockDim.x) s.ptr[i] = __ldg(ptr + d.q0 + i);
+  // independent loads first, so no warp waits on a foreign id before issuing
+  // them; the per-block pieces are 16-byte aligned and padded, so they move
+  // as 16-byte vectors
+  const int nw = (d.ne + 3) >> 2, ne4 = (d.nent + 3) >> 2, np8 = (d.np + 1 + 7) >> 3;
+  for (int i = threadIdx.x; i < nw; i += blockDim.x)
+    reinterpret_cast<float4*>(s.w)[i] = __ldg(reinterpret_cast<const float4*>(w + d.w0) + i);
+  for (int i = threadIdx.x; i < ne4; i += blockDim.x)
+    reinterpret_cast<uint4*>(s.ent)[i] = __ldg(reinterpret_cast<const uint4*>(inc + d.i0) + i);
+  for (int i = threadIdx.x; i < np8; i += blockDim.x)
+    reinterpret_cast<uint4*>(s.ptr)[i] = __ldg(reinterpret_cast<const uint4*>(ptr + d.q0) + i);
   for (int p = threadIdx.x; p < d.np; p += blockDim.x) {
     const int32_t r = flux_rec(d, flist, p);
     if (r < 0) continue;
@@ -397,11 +403,38 @@ __global__ void __launch_bounds__(1024) spmv_kernel(
   float* ws = xs + ((nx + 3) & ~3);
   uint32_t* es = reinterpret_cast<uint32_t*>(ws + ((d.ne + 3) & ~3));
   uint16_t* ps = reinterpret_cast<uint16_t*>(es + d.ne);
-  for (int i = threadIdx.x; i < d.ne; i += blockDim.x) {
-    ws[i] = __ldg(w + d.w0 + i);
-    es[i] = __ldg(inc + d.i0 + i);
+  // weights, entries and row offsets: four loads in flight per thread
+  for (int i0 = threadIdx.x; i0 < d.ne; i0 += 4 * blockDim.x) {
+    float wv[4];
+    uint32_t ev[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      wv[u] = i < d.ne ? __ldg(w + d.w0 + i) : 0.f;
+      ev[u] = i < d.ne ? __ldg(inc + d.i0 + i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      if (i < d.ne) {
+        ws[i] = wv[u];
+        es[i] = ev[u];
+      }
+    }
   }
-  for (int i = threadIdx.x; i <= ny; i += blockDim.x) ps[i] = __ldg(ptr + d.q0 + i);
+  for (int i0 = threadIdx.x; i0 <= ny; i0 += 4 * blockDim.x) {
+    uint16_t pv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      pv[u] = i <= ny ? __ldg(ptr + d.q0 + i) : (uint16_t)0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * (int)blockDim.x;
+      if (i <= ny) ps[i] = pv[u];
+    }
+  }
   // x entries: four (id, value) load chains in flight per thread
   for (int i0 = threadIdx.x; i0 < nx; i0 += 4 * blockDim.x) {
     int32_t r[4];
@@ -592,8 +625,9 @@ struct Scope {
 
 size_t flux_smem_bytes(const FluxArgs& a, int D, int copies) {
   const size_t npos = ((size_t)a.max_np + 3) & ~(size_t)3;
-  return (size_t)copies * D * npos * sizeof(float) + (size_t)a.max_ne * sizeof(float) +
-         (size_t)a.max_nent * sizeof(uint32_t) + ((size_t)a.max_np + 1) * sizeof(uint16_t) + 16;
+  const auto up = [](size_t v, size_t m) { return (v + m - 1) / m * m; };
+  return (size_t)copies * D * npos * sizeof(float) + up(a.max_ne, 4) * sizeof(float) +
+         up(a.max_nent, 4) * sizeof(uint32_t) + up((size_t)a.max_np + 1, 8) * sizeof(uint16_t) + 16;
 }
 
 template <int D>
