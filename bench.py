@@ -671,7 +671,7 @@ def main():
             from paper_1605_02043_gb300 import build as B
             import hashlib
             hh = hashlib.sha256()
-            for f in ("kernels.cu", "flux_tma.cu"):
+            for f in ("flux_tma.cu", "kernels.h", "internal.h"):  # the pipelined kernels' sources
                 hh.update(open(os.path.join(B.CSRC, f), "rb").read())
             h = hh.hexdigest()[:16]
             ent = tr.get(f"flux_fwd_C{args.C}_n{n}")
