@@ -3,10 +3,11 @@
 The paper ties C to the thread-block size and picks it by hand (Section 5,
 Table 3: blocks of 256, 512 and 1024 tasks).  Here C (tasks per schedule
 block) and the kernel organisation (pipeline stages, threads per CUDA block)
-are separate knobs, chosen by measurement: for a seeded sample of the graphs
-every candidate C is partitioned by the library, the sample is merged into
-one schedule, and one forward step plus one adjoint step is timed on the GPU
-with CUDA events for every (stages, threads) candidate.  The fastest
+are separate knobs (stages 0: one CUDA block per schedule block), chosen by
+measurement: for a seeded sample of the graphs every candidate C is
+partitioned by the library, the sample is merged into one schedule, and one
+forward step plus one adjoint step is timed on the GPU with CUDA events for
+every (stages, threads) candidate.  The fastest
 configuration per task wins.  Results are cached in a JSON file keyed by a
 hash of the sample and the candidate lists, so a rerun skips the search.
 """
@@ -22,7 +23,7 @@ import numpy as np
 from . import Schedule
 
 DEFAULT_CS = (256, 512, 1024)
-DEFAULT_KERNELS = ((3, 192), (2, 192), (3, 128), (3, 256), (2, 256))
+DEFAULT_KERNELS = ((3, 192), (2, 192), (3, 128), (3, 256), (2, 256), (0, 160), (0, 256))
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
