@@ -195,7 +195,10 @@ int ep_cost(ep_schedule *s, int64_t *loads, int64_t *vertex_cut, void *stream);
  *   EP_KERNEL_SPMV (bipartite schedule): x float[n] (read), w float[m],
  *     out float[n] = y (written), D = 1, steps = 1, tau ignored.
  * Uses schedule-owned device workspace (allocated on first use: make the
- * first call before any stream capture).
+ * first call before any stream capture).  Every kernel stages a whole
+ * schedule block in shared memory: EP_EINVAL (nothing launched) when the
+ * largest block does not fit, i.e. C too large for the graph and D (for
+ * D = 5 on mesh-like graphs, C up to a few thousand tasks fits).
  */
 int ep_run(ep_schedule *s, int32_t kernel, float *x, const float *w, float *out, int32_t D,
            int32_t steps, float tau, void *stream);

@@ -326,6 +326,18 @@ int ensure_bacc(ep_schedule* s, int32_t R, cudaStream_t st) {
 }
 
 // One forward step (edge kernel + shared-vertex fold) in schedule layout.
+// The one-block kernels stage a whole schedule block in shared memory.
+int block_fits(ep_schedule* s, size_t need) {
+  int dev = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (need + 1024 > (size_t)optin)
+    return fail(EP_EINVAL,
+                "a schedule block needs %zu bytes of shared memory (limit %d): use a smaller C",
+                need, optin - 1024);
+  return EP_OK;
+}
+
 int flux_step_any(ep_schedule* s, int32_t D, const float* w, const float* x_in, float* x_out,
                   float* out, float tau, cudaStream_t st) {
   ep::dev::FluxArgs a = flux_args(s, w, x_in, x_out, out, tau);
@@ -333,13 +345,12 @@ int flux_step_any(ep_schedule* s, int32_t D, const float* w, const float* x_in, 
     CU(ep::dev::flux_step_ldg(a, D, st));
     return EP_OK;
   }
-  if (s->stages == 0) {
-    CU(ep::dev::flux_step(a, D, st));
-    return EP_OK;
-  }
   ep::dev::TmaPlan P;
-  if (int rc = tma_plan(s, D, false, P)) return rc;
-  if (!P.fits) {
+  if (s->stages != 0) {
+    if (int rc = tma_plan(s, D, false, P)) return rc;
+  }
+  if (s->stages == 0 || !P.fits) {
+    if (int rc = block_fits(s, ep::dev::flux_block_smem(a, D, false))) return rc;
     CU(ep::dev::flux_step(a, D, st));
     return EP_OK;
   }
@@ -364,13 +375,12 @@ int flux_step_any(ep_schedule* s, int32_t D, const float* w, const float* x_in, 
 int flux_adj_any(ep_schedule* s, int32_t D, const float* w, const float* x, float* lam, float* gw,
                  float tau, cudaStream_t st) {
   ep::dev::FluxArgs a = flux_args(s, w, x, nullptr, nullptr, tau);
-  if (s->stages == 0) {
-    CU(ep::dev::flux_adjoint_step(a, D, lam, gw, st));
-    return EP_OK;
-  }
   ep::dev::TmaPlan P;
-  if (int rc = tma_plan(s, D, true, P)) return rc;
-  if (!P.fits) {
+  if (s->stages != 0) {
+    if (int rc = tma_plan(s, D, true, P)) return rc;
+  }
+  if (s->stages == 0 || !P.fits) {
+    if (int rc = block_fits(s, ep::dev::flux_block_smem(a, D, true))) return rc;
     CU(ep::dev::flux_adjoint_step(a, D, lam, gw, st));
     return EP_OK;
   }
@@ -421,6 +431,9 @@ int spmv_lay(ep_schedule* s, const float* x_lay, const float* w_lay, float* y_la
   a.tpb = s->tpb;
   a.readonly = s->cache == EP_CACHE_L1;
   a.timer = s->t();
+  if (!a.readonly) {
+    if (int rc = block_fits(s, ep::dev::spmv_block_smem(a))) return rc;
+  }
   CU(ep::dev::spmv(a, st));
   return EP_OK;
 }

@@ -809,9 +809,17 @@ __global__ void __launch_bounds__(1024) spmv_ldg_kernel(
   }
 }
 
+size_t flux_block_smem(const FluxArgs& a, int D, bool adjoint) {
+  return flux_smem_bytes(a, D, adjoint ? 2 : 1);
+}
+
+size_t spmv_block_smem(const SpmvArgs& a) {
+  return (size_t)(a.max_nx + 4) * sizeof(float) + (size_t)(a.max_ne + 4) * 8 +
+         (size_t)(a.max_ny + 1) * sizeof(uint16_t) + 16;
+}
+
 cudaError_t spmv(const SpmvArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)(a.max_nx + 4) * sizeof(float) + (size_t)(a.max_ne + 4) * 8 +
-                      (size_t)(a.max_ny + 1) * sizeof(uint16_t) + 16;
+  const size_t smem = spmv_block_smem(a);
   cudaError_t e = allow_smem(spmv_kernel, smem);
   if (e != cudaSuccess) return e;
   if (a.ny_zero > 0) {

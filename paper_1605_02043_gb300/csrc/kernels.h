@@ -95,6 +95,9 @@ cudaError_t bnd_update(const FluxArgs& a, int D, float* x_in_out, const float* x
                        cudaStream_t st);
 cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st);
 cudaError_t spmv(const SpmvArgs& a, cudaStream_t st);
+// shared memory the one-block kernels stage for the schedule's largest block
+size_t flux_block_smem(const FluxArgs& a, int D, bool adjoint);
+size_t spmv_block_smem(const SpmvArgs& a);
 // n data vertices; state planes of n_rec records
 cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x,
                       float* x_lay, cudaStream_t st, Timer* t);

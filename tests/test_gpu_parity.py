@@ -144,6 +144,37 @@ def test_flux_edge_cases():
             assert S.check_errors() == 0
 
 
+def test_large_blocks():
+    # C = 4096 still fits one block's state in shared memory; C = EP_MAX_C
+    # (16384) schedules exactly but its blocks do not fit: a clear EP_EINVAL
+    n = 1 << 16
+    src, dst = W.knn_mesh(n, 4, 0)
+    x0 = W.flux_state(n, 5, 0)
+    w = W.flux_weights(src.size, 0)
+    S = E.Schedule.partition(src, dst, n, 4096)
+    x = cuda(x0)
+    S.run(x, cuda(w), None, steps=2, tau=1e-3)
+    xT, _ = O.flux_steps(src, dst, x0, w, 2, 1e-3)
+    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
+    g = W.loss_weights(n, 5, 1)
+    lam = cuda(g)
+    gw = torch.zeros(src.size, device="cuda")
+    S.run_adjoint(cuda(x0), cuda(w), lam, gw, steps=1, tau=1e-3)
+    dx, dw = O.flux_adjoint(src, dst, x0, w, 1, 1e-3, g)
+    assert rel_l2(lam.cpu().numpy(), dx) <= RTOL and rel_l2(gw.cpu().numpy(), dw) <= RTOL
+    big = E.Schedule.partition(src, dst, n, 16384)
+    check_schedule_matches_oracle(big, O.ep_schedule(src, dst, n, 16384))
+    for stages in (3, 0):
+        big.set_pipeline(stages)
+        with pytest.raises(E.EpError) as ei:
+            big.run(cuda(x0), cuda(w), None, steps=1, tau=1e-3)
+        assert ei.value.code == -1 and "smaller C" in str(ei.value)
+    torch.cuda.synchronize()  # the context is still healthy
+    x = cuda(x0)
+    S.run(x, cuda(w), None, steps=1, tau=1e-3)
+    assert S.check_errors() == 0
+
+
 def test_layout_round_trip(small_mesh):
     src, dst, n = small_mesh
     S = E.Schedule.partition(src, dst, n, 256)
