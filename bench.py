@@ -50,8 +50,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--C", type=int, default=256)
-    ap.add_argument("--threads", type=int, default=192, help="consumer threads per CUDA block")
+    ap.add_argument("--C", type=int, default=512)
+    ap.add_argument("--threads", type=int, default=None,
+                    help="threads per CUDA block (default 256 consumer threads for the mesh, "
+                         "192 for the R-MAT SpMV)")
     ap.add_argument("--stages", type=int, default=3, help="0: one CUDA block per schedule block")
     ap.add_argument("--n", type=int, default=1 << 20, help="mesh points (default: the 1M-node mesh)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -583,6 +585,8 @@ def study_cache(torch, E, args, src, dst, x0, w, flush):
 
 def main():
     args = parse()
+    if args.threads is None:
+        args.threads = 192 if args.workload == "rmat" else 256
     if args.impl == "reference":
         run_reference(args)
         return

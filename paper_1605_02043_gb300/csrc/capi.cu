@@ -225,7 +225,7 @@ ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, f
                             float* out, float tau) {
   ep::dev::FluxArgs a;
   a.desc = s->d_desc.as<ep::FluxDesc>();
-  a.k = s->h.k;
+  a.k = (int64_t)s->h.fdesc.size();  // kernel blocks (large schedule blocks are cut)
   a.flist = s->d_flist.as<int32_t>();
   a.inc = s->d_inc.as<uint32_t>();
   a.ptr = s->d_ptr.as<uint16_t>();
@@ -302,7 +302,7 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
   int per_sm = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P.threads, P.smem));
   if (per_sm < 1) return fail(EP_EINVAL, "pipelined kernel does not fit on an SM");
-  P.grid = (int)std::min<int64_t>(h.k, (int64_t)per_sm * s->sm_count);
+  P.grid = (int)std::min<int64_t>((int64_t)h.fdesc.size(), (int64_t)per_sm * s->sm_count);
   if (!s->ws_ctl.p) {
     CU(s->ws_ctl.ensure(2 * sizeof(int)));
     CU(cudaMemset(s->ws_ctl.p, 0, 2 * sizeof(int)));

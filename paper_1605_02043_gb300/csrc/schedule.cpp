@@ -111,7 +111,7 @@ void class_order(const HostSchedule& s, int64_t b, const std::vector<int32_t>& d
   std::stable_sort(out.begin(), out.end(), [&](int32_t a, int32_t c) { return deg[a] > deg[c]; });
 }
 
-std::string flux_layout(HostSchedule& s) {
+std::string flux_layout_blocks(HostSchedule& s) {
   std::vector<int32_t> p, owner;
   usage(s, p, owner);
   s.rec_of.assign(s.nd, -1);
@@ -228,6 +228,93 @@ std::string flux_layout(HostSchedule& s) {
   while (s.wmap.size() % 4) s.wmap.push_back(-1);
   s.w_pad = (int64_t)s.wmap.size();
   return "";
+}
+
+// Kernel blocks of the flux layout.  A schedule block whose vertex set is
+// far above the typical one (more than 3/2 of the median |V_b|) is cut in
+// task order into halves, recursively, until every piece is within that
+// size; each piece is then laid out as a block of its own (vertices shared
+// by the pieces become shared vertices).  The schedule and its cost are
+// unchanged; the kernels' shared-memory stages, sized for the largest kernel
+// block, get smaller.  Returns false when no block needs cutting.
+struct Pieces {
+  int64_t k = 0;
+  std::vector<int64_t> block_ptr, vert_ptr;
+  std::vector<int32_t> vert_list;
+};
+
+bool cut_large_blocks(const HostSchedule& s, Pieces& out) {
+  if (s.k < 2) return false;
+  std::vector<int64_t> sz(s.k);
+  for (int64_t b = 0; b < s.k; ++b) sz[b] = s.vert_ptr[b + 1] - s.vert_ptr[b];
+  const int64_t biggest = *std::max_element(sz.begin(), sz.end());
+  std::nth_element(sz.begin(), sz.begin() + s.k / 2, sz.end());
+  const int64_t limit = std::max<int64_t>(64, sz[s.k / 2] * 3 / 2);
+  if (biggest <= limit) return false;
+  std::vector<int32_t> stamp(s.nd, -1);
+  int32_t piece = 0;
+  out.block_ptr.assign(1, 0);
+  out.vert_ptr.assign(1, 0);
+  out.vert_list.clear();
+  // first-touch vertex list of tasks [lo, hi) appended to out.vert_list
+  auto touch = [&](int64_t lo, int64_t hi) {
+    const size_t before = out.vert_list.size();
+    for (int64_t i = lo; i < hi; ++i) {
+      int32_t u, v;
+      task_ends(s, s.edge_perm[i], u, v);
+      if (stamp[u] != piece) {
+        stamp[u] = piece;
+        out.vert_list.push_back(u);
+      }
+      if (stamp[v] != piece) {
+        stamp[v] = piece;
+        out.vert_list.push_back(v);
+      }
+    }
+    return (int64_t)(out.vert_list.size() - before);
+  };
+  std::vector<std::pair<int64_t, int64_t>> todo;
+  for (int64_t b = 0; b < s.k; ++b) {
+    todo.assign(1, {s.block_ptr[b], s.block_ptr[b + 1]});
+    while (!todo.empty()) {  // depth first, left half first: pieces stay in task order
+      const auto [lo, hi] = todo.back();
+      todo.pop_back();
+      const size_t mark = out.vert_list.size();
+      const int64_t nv = touch(lo, hi);
+      if (nv > limit && hi - lo > 1) {
+        out.vert_list.resize(mark);
+        ++piece;  // fresh stamps for the halves
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        todo.push_back({mid, hi});
+        todo.push_back({lo, mid});
+        continue;
+      }
+      ++piece;
+      out.block_ptr.push_back(hi);
+      out.vert_ptr.push_back((int64_t)out.vert_list.size());
+    }
+  }
+  out.k = (int64_t)out.block_ptr.size() - 1;
+  return true;
+}
+
+std::string flux_layout(HostSchedule& s) {
+  Pieces pc;
+  const bool cut = cut_large_blocks(s, pc);
+  if (cut) {
+    std::swap(s.k, pc.k);
+    s.block_ptr.swap(pc.block_ptr);
+    s.vert_ptr.swap(pc.vert_ptr);
+    s.vert_list.swap(pc.vert_list);
+  }
+  std::string err = flux_layout_blocks(s);
+  if (cut) {  // the schedule itself is the uncut one
+    std::swap(s.k, pc.k);
+    s.block_ptr.swap(pc.block_ptr);
+    s.vert_ptr.swap(pc.vert_ptr);
+    s.vert_list.swap(pc.vert_list);
+  }
+  return err;
 }
 
 std::string spmv_layout(HostSchedule& s) {

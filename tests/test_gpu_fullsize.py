@@ -1,6 +1,6 @@
 """Parity at the benchmark sizes, in the launch configuration bench.py times (GPU only).
 
-* 1M-node mesh, C = 256, pipelined kernel with the bench's defaults: schedule,
+* 1M-node mesh, C = 512, pipelined kernel with the bench's defaults: schedule,
   vertex lists, relabel and cost bit-exact with the oracle; 10 explicit steps
   and the 10-step adjoint within 1e-5 relative L2 of the FP64 oracle.
 * R-MAT scale 20, C = 512, bipartite: full SpMV against the FP64 oracle; the
@@ -41,25 +41,25 @@ def cuda(a):
 def mesh1m():
     n = 1 << 20
     src, dst = W.knn_mesh(n, 4, 0)
-    S = E.Schedule.partition(src, dst, n, 256)
+    S = E.Schedule.partition(src, dst, n, 512)
     return n, src, dst, S
 
 
 def test_mesh1m_schedule_bit_exact(mesh1m):
     n, src, dst, S = mesh1m
-    ref = O.ep_schedule(src, dst, n, 256)
+    ref = O.ep_schedule(src, dst, n, 512)
     a = S.arrays()
     for key in ("block_ptr", "edge_perm", "vert_ptr", "vert_list", "relabel"):
         assert np.array_equal(a[key], ref[key]), key
     assert S.cost() == (ref["loads"], ref["cut"])
-    d = O.ep_schedule(src, dst, n, 256, default_order=True)
+    d = O.ep_schedule(src, dst, n, 512, default_order=True)
     assert ref["loads"] < 0.5 * d["loads"]
 
 
 def test_mesh1m_forward_and_adjoint(mesh1m):
     n, src, dst, S = mesh1m
     S.set_pipeline(3)
-    S.set_threads(192)
+    S.set_threads(256)
     x0 = W.flux_state(n, 5, 0)
     w = W.flux_weights(src.size, 0)
     T, tau = 10, 1e-3
