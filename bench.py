@@ -203,13 +203,19 @@ def bench_fwd(torch, E, S, x0, w, steps, warmup, flush):
     S.weights_in(wt, wl)
     for _ in range(warmup):
         S.step(D, xl, xl, wl, None, TAU)
-    S.timing(2)
+    # whole steps without per-kernel instrumentation, then a separate pass
+    # with the library's per-kernel events for the kernel times
     ms = timed_loop(torch, lambda: S.step(D, xl, xl, wl, None, TAU), steps, 0, flush)
+    S.timing(2)
+    n_instr = max(20, steps // 5)
+    timed_loop(torch, lambda: S.step(D, xl, xl, wl, None, TAU), n_instr, 0, flush)
     edge_ms, edge_n = S.timing_read(E.T_EDGE_FWD)
     bnd_ms, bnd_n = S.timing_read(E.T_BND)
     S.timing(0)
+    per_step = (edge_n + bnd_n) / n_instr  # our kernels per step (edge kernel + fold)
     return dict(ms=ms, edge_ms=edge_ms / max(edge_n, 1), edge_launches=edge_n,
-                bnd_ms=bnd_ms / max(bnd_n, 1), bnd_launches=bnd_n)
+                bnd_ms=bnd_ms / max(bnd_n, 1), bnd_launches=bnd_n,
+                launches_timed=int(round(per_step * len(ms))))
 
 
 def bench_fwd_bwd(torch, S, x0, w, iters, warmup, flush, T=10, every=5):
@@ -347,17 +353,20 @@ def bench_rmat(args):
         sch.weights_in(torch.from_numpy(w).cuda(), wl)
         for _ in range(args.warmup):
             sch.spmv(xl, wl, yl)
-        sch.timing(2)
         ms = timed_loop(torch, lambda: sch.spmv(xl, wl, yl), args.steps, 0, flush)
+        sch.timing(2)  # kernel times from a separate, instrumented pass
+        n_instr = max(20, args.steps // 5)
+        timed_loop(torch, lambda: sch.spmv(xl, wl, yl), n_instr, 0, flush)
         kms, kn = sch.timing_read(E.T_SPMV)
         sch.timing(0)
+        kn_timed = int(round(kn / n_instr * len(ms)))
         # cost-model bytes: entry + weight per task, 64-byte descriptor per block,
         # foreign ids, one 4-byte gather (x) or write-back (y) per vertex load
         alg = 8 * m + 64 * sch.k + 4 * cut + 4 * loads
         tot = max_over_ranks(torch, sum(ms))
         res[name] = dict(edge_updates_per_s=ws * m * len(ms) / (1e-3 * tot), ms_per_step=tot / len(ms),
                          kernel_ms=kms / max(kn, 1), loads=loads, vertex_cut=cut, alg_bytes=alg,
-                         alg_GBps=alg / (kms / max(kn, 1) * 1e-3) / 1e9, launches=kn)
+                         alg_GBps=alg / (kms / max(kn, 1) * 1e-3) / 1e9, launches=kn_timed)
     if rank != 0:
         return
     import oracle as O
@@ -701,7 +710,7 @@ def main():
                      "launch_ms": fwd["edge_ms"], "peak_kind": f"{peak_kind} HBM copy"},
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": fwd["edge_launches"] + fwd["bnd_launches"],
+        "gpu_launches": fwd["launches_timed"],
         "clocks": clk,
         "partitioned": {"edge_updates_per_s": value, "loads": loads, "vertex_cut": cut,
                         "edge_kernel_ms": fwd["edge_ms"], "bnd_kernel_ms": fwd["bnd_ms"],

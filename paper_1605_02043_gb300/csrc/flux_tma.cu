@@ -340,6 +340,9 @@ __device__ __forceinline__ void pipeline(const FluxDesc* __restrict__ desc,
                                          int* __restrict__ err, const TmaLayout L, Consume consume) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+  // launched with programmatic serialisation: wait for the previous kernel
+  // on the stream (its writes to x, lam and the accumulators) first
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ int done;  // schedule blocks finished by the consumers
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nspec = L.ahead > 0 ? 2 : 1;                 // producer (+ prefetch) warps
@@ -550,20 +553,38 @@ __global__ void __launch_bounds__(1024) flux_adj_tma_kernel(
   pipeline<D, true>(desc, flist, inc, ptr, w, x, lam, n_rec, k, err, L, consume);
 }
 
+// Launch configuration with programmatic stream serialisation: the kernel may
+// be scheduled while the previous kernel on the stream drains; it waits for
+// that kernel's completion (griddepcontrol.wait) before touching memory.
+struct PdlConfig {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  PdlConfig(dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+};
+
 template <int D>
 cudaError_t launch_fwd(const FluxArgs& a, const TmaPlan& P, cudaStream_t st) {
-  auto kern = flux_fwd_tma_kernel<D>;  // shared-memory limit raised when the plan was made
-  kern<<<P.grid, P.threads, P.smem, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w, a.x_in, a.x_out, a.bacc,
-                                          a.out, a.n_rec, a.n_int, a.n_bnd, a.tau, a.k, P.err, P.L);
-  return cudaGetLastError();
+  PdlConfig c(P.grid, P.threads, P.smem, st);  // shared-memory limit raised when the plan was made
+  return cudaLaunchKernelEx(&c.cfg, flux_fwd_tma_kernel<D>, a.desc, a.flist, a.inc, a.ptr, a.w,
+                            a.x_in, a.x_out, a.bacc, a.out, a.n_rec, a.n_int, a.n_bnd, a.tau, a.k,
+                            P.err, P.L);
 }
 
 template <int D>
 cudaError_t launch_adj(const FluxArgs& a, const TmaPlan& P, float* lam, float* gw, cudaStream_t st) {
-  auto kern = flux_adj_tma_kernel<D>;  // shared-memory limit raised when the plan was made
-  kern<<<P.grid, P.threads, P.smem, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w, a.x_in, lam, gw, a.bacc,
-                                          a.n_rec, a.n_int, a.n_bnd, a.tau, a.k, P.err, P.L);
-  return cudaGetLastError();
+  PdlConfig c(P.grid, P.threads, P.smem, st);
+  return cudaLaunchKernelEx(&c.cfg, flux_adj_tma_kernel<D>, a.desc, a.flist, a.inc, a.ptr, a.w,
+                            (const float*)a.x_in, lam, gw, a.bacc, a.n_rec, a.n_int, a.n_bnd, a.tau,
+                            a.k, P.err, P.L);
 }
 
 }  // namespace

@@ -301,6 +301,9 @@ template <int D>
 __global__ void bnd_update_kernel(const float* x_in, float* x_out, float* __restrict__ bacc,
                                   float* __restrict__ out, int64_t n_rec, int64_t n_int,
                                   int64_t n_bnd, float tau) {
+  // launched with programmatic serialisation after the edge kernel: wait for
+  // it (the accumulators and interior records it wrote) before reading
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bnd;
        i += (int64_t)gridDim.x * blockDim.x) {
     float a[D], x[D];
@@ -747,11 +750,22 @@ cudaError_t bnd_update(const FluxArgs& a, int D, float* x_out, const float* x_in
   if (a.n_bnd <= 0) return cudaSuccess;
   Scope sc(a.timer, T_BND, st);
   const int g = grid_for(a.n_bnd, 256);
-#define EP_BU(DD) \
-  bnd_update_kernel<DD><<<g, 256, 0, st>>>(x_in, x_out, a.bacc, out, a.n_rec, a.n_int, a.n_bnd, a.tau)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaSuccess;
+#define EP_BU(DD)                                                                        \
+  e = cudaLaunchKernelEx(&cfg, bnd_update_kernel<DD>, x_in, x_out, a.bacc, out, a.n_rec, \
+                         a.n_int, a.n_bnd, a.tau)
   EP_DISPATCH_D(D, EP_BU)
 #undef EP_BU
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st) {
