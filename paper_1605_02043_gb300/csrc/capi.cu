@@ -136,7 +136,7 @@ struct ep_schedule {
   int tpb = 192;
   bool bacc_dirty = true;
   // device copy of the schedule
-  DBuf d_desc, d_flist, d_ylist, d_loc, d_inc, d_ptr, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
+  DBuf d_desc, d_flist, d_ylist, d_inc, d_ptr, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
       d_ev;
   // workspace
   DBuf ws_x, ws_out, ws_w, ws_bacc, ws_lam, ws_gw, ws_hist, ws_flags, ws_cnt;

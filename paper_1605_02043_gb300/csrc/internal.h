@@ -91,8 +91,6 @@ struct HostSchedule {
   std::vector<uint32_t> sinc;   // SpMV row entries
   std::vector<uint16_t> sptr;   // SpMV row offsets
   int32_t max_nx = 0, max_ny = 0;
-
-  std::vector<uint32_t> loc;  // per task in edge_perm order: slot(u) | slot(v) << 16
 };
 
 // prescreen.cpp: checks made before partitioning (Section 4 workflow).

@@ -9,7 +9,9 @@
 //   cost             loads = sum_b |V_b|, vertex cut = loads - touched (Eq. 1);
 //   kernel layout    the cpack order split into vertices one block uses
 //                    (updated in place by that block) and shared vertices
-//                    (accumulated by atomics), plus 16-bit local slots per task.
+//                    (accumulated by atomics), with per-block descriptors,
+//                    incidence lists in shared-memory positions, foreign-id
+//                    lists and padded weights (flux), or row lists (SpMV).
 #include <algorithm>
 #include <climits>
 #include <thread>
@@ -150,7 +152,6 @@ std::string flux_layout_blocks(HostSchedule& s) {
   s.flist.clear();
   s.inc.clear();
   s.ptr.clear();
-  s.loc.clear();
   s.max_nv = 0;
   s.max_nent = 0;
   s.max_nf = 0;
@@ -367,7 +368,6 @@ std::string spmv_layout(HostSchedule& s) {
   s.sinc.clear();
   s.sptr.clear();
   s.wmap.clear();
-  s.loc.clear();
   s.max_nx = s.max_ny = 0;
   s.max_nent = 0;
   std::vector<int32_t> pos(s.nd, -1), cnt;
