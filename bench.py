@@ -282,6 +282,29 @@ def cpu_baseline(src, dst, x0, w, seconds):
                 sample=f"{steps} FP64 NumPy flux steps of the full mesh ({src.size} tasks), single thread")
 
 
+def cpu_fair(src, dst, x0, w, n, seconds):
+    """All host cores, FP64 (oracle/cpu_fair.c, OpenMP); None where it cannot be built."""
+    import oracle as O
+
+    try:
+        F = O.FairCpu(src, dst, n, D)
+    except (RuntimeError, ValueError):
+        return None
+    x = np.ascontiguousarray(x0, np.float64)
+    F.steps(x, w, 1, TAU)  # warm-up
+    t0 = time.perf_counter()
+    steps = used = 0
+    while True:
+        _, used = F.steps(x, w, 1, TAU)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return dict(value=src.size * steps / el, unit=UNIT, cores=used, kind="openmp-fp64",
+                sample=f"{steps} FP64 flux steps of the full mesh on {used} threads (pull form, "
+                       f"one vertex per loop iteration)")
+
+
 def spmv_time(torch, E, sch, x0, w, n, steps, warmup, flush):
     """Mean SpMV kernel time (ms) and step time (ms) on schedule-layout buffers."""
     xl = torch.empty(n, device="cuda")
@@ -696,6 +719,7 @@ def main():
     if rank != 0:
         return
     cpu = cpu_baseline(src, dst, x0, w, args.cpu_seconds) if ws == 1 else None
+    fair = cpu_fair(src, dst, x0, w, n, min(5.0, args.cpu_seconds)) if ws == 1 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot / len(fwd["ms"]), "higher_is_better": True,
@@ -709,6 +733,7 @@ def main():
                      "algorithmic_bytes_per_launch": alg,
                      "launch_ms": fwd["edge_ms"], "peak_kind": f"{peak_kind} HBM copy"},
         "cpu_baseline": cpu,
+        "cpu_all_cores": fair,
         "e2e": e2e,
         "gpu_launches": fwd["launches_timed"],
         "clocks": clk,

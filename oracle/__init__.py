@@ -9,6 +9,8 @@ imports it and shares no code with it.
   (Section 3.2 transform, Definition 4 reconstruction, Section 4.1 cpack,
   Eq. 1 cost).
 * Edge kernels, time stepping and the adjoint: NumPy float64 below.
+* ``cpu_fair.c``: the same explicit steps in FP64 on all host cores (OpenMP),
+  only for the bench's CPU context line; checked against the NumPy oracle.
 
 Parity status: the partition heuristic's tie-break output is a rule of this
 project (the paper delegates to METIS); beyond the worked example and the
@@ -43,6 +45,61 @@ def build() -> str:
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _SO)
     return _SO
+
+
+_FAIR_SRC = os.path.join(_HERE, "cpu_fair.c")
+_FAIR_SO = os.path.join(_BUILD, "libcpufair.so")
+
+
+def build_fair() -> str | None:
+    """Compile the OpenMP CPU baseline (cpu_fair.c); None if the compiler
+    cannot (it is optional: only the bench's CPU context line uses it)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not os.path.exists(_FAIR_SO) or os.path.getmtime(_FAIR_SO) < os.path.getmtime(_FAIR_SRC):
+        tmp = _FAIR_SO + f".{os.getpid()}.tmp"
+        try:
+            subprocess.check_call(["gcc", "-O2", "-fopenmp", "-std=c99", "-shared", "-fPIC", "-o",
+                                   tmp, _FAIR_SRC], stderr=subprocess.DEVNULL)
+        except (OSError, subprocess.CalledProcessError):
+            return None
+        os.replace(tmp, _FAIR_SO)
+    return _FAIR_SO
+
+
+class FairCpu:
+    """Multi-threaded FP64 explicit flux steps on all host cores (cpu_fair.c)."""
+
+    def __init__(self, src, dst, n: int, D: int):
+        so = build_fair()
+        if so is None:
+            raise RuntimeError("cpu_fair.c could not be built (no OpenMP)")
+        lib = ctypes.CDLL(so)
+        P = ctypes.c_void_p
+        lib.fair_build.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]
+        lib.fair_build.restype = P
+        lib.fair_free.argtypes = [P]
+        lib.fair_steps.argtypes = [P, P, P, P, P, P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
+        lib.fair_steps.restype = ctypes.c_int
+        self._lib = lib
+        self.src, self.dst = _edges(src, dst)
+        self.n, self.D = n, D
+        self._h = lib.fair_build(_p(self.src), _p(self.dst), self.src.size, n, D)
+        if not self._h:
+            raise ValueError("fair_build failed")
+
+    def steps(self, x, w, steps: int, tau: float, threads: int = 0):
+        """x float64 [D][n] updated in place; returns (flux of the last step, threads used)."""
+        assert x.dtype == np.float64 and x.flags.c_contiguous and x.shape == (self.D, self.n)
+        w = np.ascontiguousarray(w, np.float64)
+        out = np.zeros_like(x)
+        used = self._lib.fair_steps(self._h, _p(self.src), _p(self.dst), _p(w), _p(x), _p(out),
+                                    steps, tau, threads)
+        return out, used
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.fair_free(self._h)
+            self._h = None
 
 
 def _load():
