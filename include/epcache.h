@@ -19,7 +19,12 @@
  *     current device; the library never frees caller memory;
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream); device work is enqueued on it and the call returns without
- *     synchronising unless stated otherwise;
+ *     synchronising unless stated otherwise.  The edge kernels and the
+ *     shared-vertex fold are launched with programmatic stream
+ *     serialisation and wait for the preceding kernel's completion before
+ *     touching memory; a caller kernel placed just before them that signals
+ *     its dependents early (griddepcontrol.launch_dependents) must have
+ *     written its results by then;
  *   - a schedule owns its host arrays, its device copy and its device
  *     workspace.  Calls on one schedule must not overlap in time (they share
  *     that workspace); distinct schedules are independent.
