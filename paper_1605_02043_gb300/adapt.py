@@ -76,7 +76,7 @@ class Policy:
 
 
 class AdaptiveFlux:
-    """Repeated explicit flux steps (Eq. 2 kernel) under EP-adapt.
+    """Repeated explicit flux steps (the cfd interaction of Section 1) under EP-adapt.
 
     x: CUDA float32 (D, n) initial state, w: CUDA float32 (m,) task weights,
     both in the caller's order.  The state stays resident in the current
