@@ -192,7 +192,12 @@ int ep_cost_host(const ep_schedule *s, int64_t *loads, int64_t *vertex_cut);
 int ep_cost(ep_schedule *s, int64_t *loads, int64_t *vertex_cut, void *stream);
 
 /*
- * Forward run in the caller's layout (device pointers):
+ * Forward run in the caller's layout (device pointers).  The edge kernel is the
+ * software-cache kernel of Section 4 (Fig. 7(d)) run under the schedule of
+ * Section 3.2; the flux interaction is the particle kernel of the cfd example
+ * of Section 1, SpMV the y = A x of Section 5.2 on the bipartite graph of
+ * Definition 1.  The explicit time step x <- x + tau*flux has no counterpart
+ * in the paper: it is this library's workload definition.
  *   EP_KERNEL_FLUX: x float[D][n] (in: x_0, out: x_T), w float[m] (task
  *     order), out float[D][n] or NULL (receives flux(x_{T-1})), 1 <= D <=
  *     EP_MAX_D, steps = T >= 1 explicit steps x_{t+1} = x_t + tau*flux(x_t).
@@ -209,6 +214,7 @@ int ep_run(ep_schedule *s, int32_t kernel, float *x, const float *w, float *out,
            int32_t steps, float tau, void *stream);
 
 /*
+ * No counterpart in the paper (a host-buffer convenience of this library).
  * Same as ep_run with HOST pointers (x in/out, w in, out optional): copies
  * inputs to the device, runs, copies results back and synchronises.
  */
@@ -216,6 +222,10 @@ int ep_run_host(ep_schedule *s, int32_t kernel, float *x, const float *w, float 
                 int32_t steps, float tau, void *stream);
 
 /*
+ * No counterpart in the paper: the reverse-mode derivative of the explicit
+ * flux steps for a linear loss L = <g, x_T> (lam = g on entry), this library's
+ * training pattern.  It runs over the same schedule and with the same access
+ * pattern as the forward kernel of Section 4.
  * Reverse sweep of `steps` flux steps started from x0 (device, float[D][n],
  * caller layout): recomputes x_0..x_{T-1} into workspace, then for t = T-1..0
  *   gbar_e = lam_u - lam_v, d = x_v - x_u, s = |d|^2,
@@ -229,33 +239,45 @@ int ep_run_adjoint(ep_schedule *s, const float *x0, const float *w, float *lam, 
 
 /* ----------------------------------------------------- schedule layout API
  * The kernels work on the schedule's own layout (the paper's opt_arrayA,
- * Section 4.1): records in cpack order with the vertices used by one block
- * only placed first, and the D components of every record split into planes
- * of width 4, 2 and 1 (D = 4a + 2b + c): plane k is a contiguous array of
- * n_rec records of its width, so a buffer is n_rec * D floats, unpadded.
- * Task weights use ep_weights_floats(s) floats (edge_perm order, padded per
- * block).  Keeping state in this layout across calls avoids the permutations.
+ * Section 4.1, rearranged for bulk copies): for every kernel block, in block
+ * order, one contiguous run of state records holding first the vertices that
+ * only this block uses, then the block's own copy of every shared vertex it
+ * uses (a shared vertex has one record per block that uses it; all copies
+ * hold the same value between calls); the untouched vertices follow.  The D
+ * components of every record are split into planes of width 4, 2 and 1
+ * (D = 4a + 2b + c): plane k is a contiguous array of n_rec records of its
+ * width, so a buffer is n_rec * D floats.  Flux schedules (the forward
+ * kernels read every task from both of its endpoints) keep one weight per
+ * incidence slot, two per task; SpMV schedules one per task.  Keeping state
+ * in this layout across calls avoids the permutations.
  */
 int32_t ep_record_floats(int32_t D);
 /* Floats needed for one state buffer in schedule layout (n_records * D). */
 int64_t ep_layout_floats(const ep_schedule *s, int32_t D);
-/* x_lay <- x (caller layout float[D][n]). */
+/* x_lay <- x (caller layout float[D][n]); every copy of a shared vertex is
+ * written, padding records get 0. */
 int ep_layout_in(ep_schedule *s, int32_t D, const float *x, float *x_lay, void *stream);
 /* x <- x_lay (caller layout float[D][n]). */
 int ep_layout_out(ep_schedule *s, int32_t D, const float *x_lay, float *x, void *stream);
-/* Floats of a task-weight buffer in schedule layout: tasks in edge_perm order,
- * each block's run starting on a 16-byte boundary (zero-filled padding
- * between runs). */
+/* Floats of a task-weight buffer in schedule layout: flux schedules one slot
+ * per task endpoint (sliced per block, see ep_step), SpMV schedules the tasks
+ * in edge_perm order; every block's run starts on a 16-byte boundary. */
 int64_t ep_weights_floats(const ep_schedule *s);
-/* w_lay <- w permuted into schedule layout (padding slots get 0). */
+/* w_lay <- w permuted into schedule layout: every slot of a task gets its
+ * weight, padding slots get 0. */
 int ep_weights_in(ep_schedule *s, const float *w, float *w_lay, void *stream);
-/* w[task] += w_lay[slot of task] for every task (padding slots ignored). */
+/* w[task] += w_lay[slot] for every task, from one slot per task: its only
+ * slot (SpMV), or the slot at its first endpoint (flux), which is where
+ * ep_adjoint_step accumulates the weight gradient. */
 int ep_weights_out_add(ep_schedule *s, const float *w_lay, float *w, void *stream);
 
 /*
  * One explicit flux step in schedule layout: x_out = x_in + tau*flux(x_in)
  * (x_out may equal x_in), out_lay = flux(x_in) if not NULL.  Two kernel
- * launches; uses schedule-owned boundary accumulators (zero between calls).
+ * launches: the edge kernel updates the vertices only one kernel block uses
+ * in place and adds the partial flux of the shared ones into schedule-owned
+ * accumulators (zero between calls); the fold then writes x + tau * flux to
+ * every copy of each shared vertex and clears its accumulator.
  */
 int ep_step(ep_schedule *s, int32_t D, const float *x_in, float *x_out, const float *w_lay,
             float *out_lay, float tau, void *stream);
@@ -279,6 +301,10 @@ int ep_adjoint_step(ep_schedule *s, int32_t D, const float *x_lay, const float *
                     float *grad_w_lay, float tau, void *stream);
 
 /*
+ * No counterpart in the paper (a build-side pattern of this library): the
+ * union of balanced edge partitions of disjoint affinity graphs (Definition 1)
+ * is an edge partition of their union, and its cost (Eq. 1) is the sum of the
+ * parts' costs, so many small graphs can share one launch.
  * Merge independent schedules (disjoint graphs, e.g. many meshes) into one
  * schedule whose blocks run in a single launch.  Vertex ids of part i are
  * offset by the sum of the n of parts 0..i-1, task ids likewise by m.  The
@@ -312,18 +338,18 @@ int ep_timing_read(ep_schedule *s, int32_t kernel_class, double *total_ms, int64
 int ep_set_threads(ep_schedule *s, int32_t threads);
 
 /*
- * Edge-kernel organisation for flux steps.  stages = 0: one CUDA block per
- * schedule block (stage, compute, write back).  stages = 2..4 (default 3):
- * persistent CUDA blocks; a producer warp fills a ring of that many
- * shared-memory stages with 1-D TMA bulk copies of each schedule block's
- * contiguous pieces; with ahead > 0 (0..64, default 0) a second warp pulls
- * the schedule block `ahead` positions later into L2; consumer warps
- * (ep_set_threads) gather foreign records with cp.async and compute one
- * stage while the next ones load.  Results agree up to FP32 rounding order.
- * When two stages of the schedule's largest block do not fit in shared
- * memory, launches use the stages = 0 kernel instead.
+ * Edge-kernel organisation for flux steps (the software cache of Section 4).
+ * stages = 0: one CUDA block per kernel block (stage, compute, write back).
+ * stages = 2..8 (default 3): persistent CUDA blocks; a producer thread fills a
+ * ring of that many shared-memory stages with 1-D TMA bulk copies of each
+ * kernel block's contiguous pieces (its record run, slots, weights, shared
+ * ids); consumer warps (ep_set_threads, at most 992 of them are used) take
+ * whole slices of 32 positions and compute one stage while the next ones
+ * load.  Results agree up to FP32 rounding order.  Fewer stages are used when
+ * that many do not fit in shared memory; when two do not fit, launches use the
+ * stages = 0 kernel instead.
  */
-int ep_set_pipeline(ep_schedule *s, int32_t stages, int32_t ahead);
+int ep_set_pipeline(ep_schedule *s, int32_t stages);
 
 /*
  * Reads and clears the error word of the pipelined kernels (synchronises
@@ -361,16 +387,19 @@ int ep_set_cache(ep_schedule *s, int32_t mode);
  */
 int ep_debug_stall(ep_schedule *s, int32_t block_index);
 
+/* No counterpart in the paper (resource release): frees a schedule, its host
+ * arrays, its device copy and its workspace.  NULL is ignored.  The caller
+ * must make sure no kernel enqueued on the schedule is still running. */
 void ep_schedule_free(ep_schedule *s);
 
 /* ---------------------------------------------------- no-allocation variant
- * The paper has no counterpart to this entry point; it exists for callers
- * that cannot let a library allocate device memory: code that runs while a
- * stream is being captured into a CUDA graph (cudaMalloc is not permitted
- * there), applications that own all device memory through their own pool,
- * and loops that cannot afford the device synchronisation an allocation may
- * cause.  It computes what ep_cost() computes, from caller-owned device
- * arrays, and allocates nothing:
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot let a library allocate device memory: applications that hand all
+ * device memory to their own pool or framework allocator and forbid
+ * allocations behind its back, and latency-bound loops that cannot take the
+ * implicit device synchronisation that cudaMalloc and cudaFree may cause.  It
+ * computes what ep_cost() computes, from caller-owned device arrays, and
+ * allocates nothing:
  *   block_ptr  device int64[k+1]: tasks of block b are positions
  *              [block_ptr[b], block_ptr[b+1]) of eu/ev
  *   eu, ev     device int32[m]: the two data-vertex ids of every task, in
@@ -378,17 +407,26 @@ void ep_schedule_free(ep_schedule *s);
  *   max_ne     largest block_ptr[b+1] - block_ptr[b], 1..EP_MAX_C
  *   counts     device uint64[2], written: [0] = loads = sum_b |V_b|,
  *              [1] = number of distinct vertices (vertex cut = [0] - [1])
+ * The device arrays cannot be checked on the host, so misuse is reported in
+ * `counts` itself: if any block is longer than max_ne (or block_ptr
+ * decreases), or any id lies outside [0, nd), counts[0] is set to
+ * EP_NOALLOC_INVALID and counts[1] holds the reasons (EP_NOALLOC_BAD_BLOCK,
+ * EP_NOALLOC_BAD_ID, or both); the return value is still EP_OK, because the
+ * call does not wait for its kernels.
  * Its only scratch is a fixed array of EP_NOALLOC_MAX_VERTICES one-byte
- * flags in the library's device memory, which every GPU that loads this part
- * of the library keeps until the process exits.  nd above that limit gives
- * EP_EINVAL.  The first call on a device looks up that array's address
- * (make the first call before any stream capture).  All calls share the
- * array, so calls whose kernels overlap on the GPU race with each other;
- * each call clears the flags it uses before counting.  Enqueued on `stream`,
- * no synchronisation.  Errors: EP_EINVAL, EP_ENODEV, EP_ECUDA, with a
- * message from ep_noalloc_last_error().
+ * flags plus a status word in the library's device memory, which every GPU
+ * that loads this part of the library keeps until the process exits.  nd
+ * above that limit gives EP_EINVAL.  The first call on a device looks up that
+ * array's device address.  All calls share the array, so calls whose kernels
+ * overlap on the GPU race with each other; each call clears the flags and the
+ * status word it uses before counting.  Enqueued on `stream`, no
+ * synchronisation.  Errors: EP_EINVAL, EP_ENODEV, EP_ECUDA, with a message
+ * from ep_noalloc_last_error().
  */
 #define EP_NOALLOC_MAX_VERTICES (1 << 24)
+#define EP_NOALLOC_INVALID 0xffffffffffffffffull /* counts[0] of a misused call */
+#define EP_NOALLOC_BAD_BLOCK 1u /* counts[1] bit: a block longer than max_ne */
+#define EP_NOALLOC_BAD_ID 2u    /* counts[1] bit: an id outside [0, nd) */
 int ep_cost_noalloc(const int64_t *block_ptr, const int32_t *eu, const int32_t *ev, int64_t k,
                     int64_t nd, int32_t max_ne, unsigned long long *counts, void *stream);
 const char *ep_noalloc_last_error(void);

@@ -214,10 +214,10 @@ class Schedule:
     def set_threads(self, threads: int):
         check(lib().ep_set_threads(self._h, threads))
 
-    def set_pipeline(self, stages: int, ahead: int = 0):
-        """0: one CUDA block per schedule block; 2..4: persistent pipelined kernel
-        with `ahead` schedule blocks of L2 prefetch."""
-        check(lib().ep_set_pipeline(self._h, stages, ahead))
+    def set_pipeline(self, stages: int):
+        """0: one CUDA block per kernel block; 2..8: persistent pipelined kernel
+        with that many shared-memory stages."""
+        check(lib().ep_set_pipeline(self._h, stages))
 
     def check_errors(self, stream=None) -> int:
         """Error word of the pipelined kernels (raises EpError when non-zero)."""

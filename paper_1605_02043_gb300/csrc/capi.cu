@@ -15,6 +15,7 @@
 
 #include "epcache.h"
 #include "internal.h"
+#include "flux_common.cuh"
 #include "kernels.h"
 
 namespace {
@@ -138,13 +139,13 @@ struct ep_schedule {
   // device copy of the schedule
   DBuf d_desc, d_flist, d_ylist, d_inc, d_ptr, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
       d_ev;
+  DBuf d_sidx, d_soff, d_sid, d_cptr, d_crec, d_vrec, d_gslot;  // flux layout
   // workspace
   DBuf ws_x, ws_out, ws_w, ws_bacc, ws_lam, ws_gw, ws_hist, ws_flags, ws_cnt;
   DBuf ws_hx, ws_hw, ws_hout;
   EventTimer timer;
   ep::dev::Timer* t() { return timer.on ? &timer : nullptr; }
   int stages = 3;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
-  int ahead = 0;   // L2 prefetch distance of the pipelined kernels, in schedule blocks per CUDA block
   int stall = -1;  // test hook of the bounded waits (ep_debug_stall)
   int cache = EP_CACHE_SMEM;  // forward flux kernel family (ep_set_cache)
   DBuf ws_ctl;     // [0] block counter, [1] error word
@@ -204,9 +205,13 @@ int ensure_device(ep_schedule* s) {
     CU(upload(s->d_yrec, h.yrec_of));
   } else {
     CU(upload(s->d_desc, h.fdesc));
-    CU(upload(s->d_flist, h.flist));
-    CU(upload(s->d_inc, h.inc));
-    CU(upload(s->d_ptr, h.ptr));
+    CU(upload(s->d_sidx, h.sidx));
+    CU(upload(s->d_soff, h.soff));
+    CU(upload(s->d_sid, h.sid_list));
+    CU(upload(s->d_cptr, h.cptr));
+    CU(upload(s->d_crec, h.crec));
+    CU(upload(s->d_vrec, h.vrec));
+    CU(upload(s->d_gslot, h.gslot));
     CU(upload(s->d_wmap, h.wmap));
     CU(upload(s->d_rec, h.rec_of));
   }
@@ -216,8 +221,8 @@ int ensure_device(ep_schedule* s) {
 
 cudaStream_t as_stream(void* p) { return static_cast<cudaStream_t>(p); }
 
-// weight layout: flux schedules use the padded per-block layout (wmap),
-// SpMV schedules the plain schedule order (edge_perm)
+// weight layout: flux schedules one weight per slot (two per task), SpMV
+// schedules one per task, both padded per block (wmap: slot -> task)
 const int32_t* wmap_of(ep_schedule* s) { return s->d_wmap.as<int32_t>(); }
 int64_t wlen_of(const ep_schedule* s) { return s->h.w_pad; }
 
@@ -226,21 +231,23 @@ ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, f
   ep::dev::FluxArgs a;
   a.desc = s->d_desc.as<ep::FluxDesc>();
   a.k = (int64_t)s->h.fdesc.size();  // kernel blocks (large schedule blocks are cut)
-  a.flist = s->d_flist.as<int32_t>();
-  a.inc = s->d_inc.as<uint32_t>();
-  a.ptr = s->d_ptr.as<uint16_t>();
+  a.sidx = s->d_sidx.as<uint16_t>();
+  a.soff = s->d_soff.as<uint16_t>();
+  a.sid = s->d_sid.as<int32_t>();
   a.w = w;
   a.x_in = x_in;
   a.x_out = x_out;
   a.bacc = s->ws_bacc.as<float>();
   a.out = out;
+  a.cptr = s->d_cptr.as<int32_t>();
+  a.crec = s->d_crec.as<int32_t>();
   a.n_rec = s->h.n_rec;
-  a.n_int = s->h.n_int;
-  a.n_bnd = s->h.n_bnd;
+  a.n_sh = s->h.n_sh;
   a.tau = tau;
-  a.max_np = s->h.max_nv;
-  a.max_ne = s->h.max_ne;
-  a.max_nent = s->h.max_nent;
+  a.max_nv = s->h.max_nv;
+  a.max_nslot = s->h.max_nslot;
+  a.max_nsh = s->h.max_nsh;
+  a.max_nsl = s->h.max_nsl;
   a.tpb = s->tpb;
   a.timer = s->t();
   return a;
@@ -249,9 +256,9 @@ ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, f
 int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P);
 
 // Stage layout and grid of the pipelined kernels for state width D (cached;
-// recomputed when the stage count, look-ahead or thread count changes).
+// recomputed when the stage count, thread count or stall hook changes).
 int tma_plan(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
-  const int key = 1 + s->stages + 8 * s->ahead + 1024 * s->tpb + (1 << 22) * (s->stall + 1);
+  const int key = 1 + s->stages + 16 * s->tpb + (1 << 16) * (s->stall + 1);
   if (s->plan_key[D][adjoint] != key) {
     if (int rc = tma_plan_compute(s, D, adjoint, s->plans[D][adjoint])) return rc;
     s->plan_key[D][adjoint] = key;
@@ -262,17 +269,8 @@ int tma_plan(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
 
 int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
   const ep::HostSchedule& h = s->h;
-  auto up = [](int64_t x, int64_t m) { return (x + m - 1) / m * m; };
   ep::dev::TmaLayout& L = P.L;
-  L.npos = (int)up(h.max_nv, 4);
-  const int64_t xb = (int64_t)D * L.npos * 4;
-  L.off_lam = (int)xb;
-  L.off_w = (int)(L.off_lam + (adjoint ? xb : 0));
-  L.off_ent = (int)(L.off_w + up(h.max_ne, 4) * 4);
-  L.off_ptr = (int)(L.off_ent + up(h.max_nent, 4) * 4);
-  L.off_flist = (int)(L.off_ptr + up(h.max_nv + 1, 8) * 2);
-  L.off_desc = (int)(L.off_flist + up(h.max_nf, 4) * 4);
-  L.stage_bytes = (int)up(L.off_desc + (int64_t)sizeof(ep::FluxDesc) + 16, 128);
+  L = ep::dev::tma_layout(flux_args(s, nullptr, nullptr, nullptr, nullptr, 0.f), D, adjoint);
   if (!s->sm_count) {
     int dev = 0;
     CU(cudaGetDevice(&dev));
@@ -282,14 +280,13 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   L.stages = std::min(s->stages, ep::dev::kMaxStages);
-  L.ahead = s->ahead;
   L.stall = s->stall;
   optin -= 1024;  // room for the kernel's static shared memory
   while (L.stages > 2 && (int64_t)L.stages * L.stage_bytes > optin) --L.stages;
   P.fits = (int64_t)L.stages * L.stage_bytes <= optin;
   if (!P.fits) return EP_OK;  // the launch falls back to one CUDA block per schedule block
   P.smem = (size_t)L.stages * L.stage_bytes;
-  P.threads = 32 * (L.ahead > 0 ? 2 : 1) + s->tpb;  // producer (+ prefetch) warp, consumer warps
+  P.threads = 32 + std::min(s->tpb, 992);  // producer warp, consumer warps
   const void* kern = ep::dev::flux_tma_kernel_ptr(D, adjoint);
   // the limit is a per-kernel attribute shared by every schedule: open it to
   // the device maximum (the launch still asks for P.smem)
@@ -312,8 +309,8 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
 }
 
 // boundary accumulators: allocated, zero
-int ensure_bacc(ep_schedule* s, int32_t R, cudaStream_t st) {
-  const size_t bytes = (size_t)s->h.n_bnd * R * sizeof(float);
+int ensure_bacc(ep_schedule* s, int32_t D, cudaStream_t st) {
+  const size_t bytes = (size_t)s->h.n_sh * ep::dev::acc_stride(D) * sizeof(float);
   if (s->ws_bacc.bytes < bytes || !s->ws_bacc.p) {
     CU(s->ws_bacc.ensure(bytes));
     s->bacc_dirty = true;
@@ -822,7 +819,7 @@ int ep_layout_in(ep_schedule* s, int32_t D, const float* x, float* x_lay, void* 
   if (!x || !x_lay) return fail(EP_EINVAL, "null argument");
   if (misaligned(x_lay)) return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
-  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), s->h.nd, s->h.n_rec, D, x, x_lay,
+  CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), s->h.nd, s->h.n_rec, D, x, x_lay,
                         as_stream(stream), s->t()));
   return EP_OK;
 }
@@ -851,7 +848,10 @@ int ep_weights_out_add(ep_schedule* s, const float* w_lay, float* w, void* strea
   g_error.clear();
   if (!s) return fail(EP_EINVAL, "null schedule");
   if (int rc = ensure_device(s)) return rc;
-  CU(ep::dev::scatter_add(wmap_of(s), wlen_of(s), w_lay, w, as_stream(stream), s->t()));
+  if (bipartite(s))
+    CU(ep::dev::scatter_add(wmap_of(s), wlen_of(s), w_lay, w, as_stream(stream), s->t()));
+  else  // the source-side slot of every task holds its value
+    CU(ep::dev::gather_add(s->d_gslot.as<int32_t>(), s->h.m, w_lay, w, as_stream(stream), s->t()));
   return EP_OK;
 }
 
@@ -864,16 +864,19 @@ int ep_step(ep_schedule* s, int32_t D, const float* x_in, float* x_out, const fl
     return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
   cudaStream_t st = as_stream(stream);
-  const int32_t R = ep::record_floats(D);
-  if (int rc = ensure_bacc(s, R, st)) return rc;
-  if (out_lay && s->h.n_rec > s->h.n_int + s->h.n_bnd) {
-    // untouched records get a zero flux, plane by plane
-    const int64_t t = s->h.n_int + s->h.n_bnd, nr = s->h.n_rec;
+  if (int rc = ensure_bacc(s, D, st)) return rc;
+  const int64_t t = s->h.n_run, nr = s->h.n_rec;
+  if (nr > t) {
+    // untouched records: zero flux, and the state carried over when out of place
     int32_t first[4], width[4];
     const int np = ep::planes_of(D, first, width);
-    for (int k = 0; k < np; ++k)
-      CU(cudaMemsetAsync(out_lay + first[k] * nr + t * width[k], 0,
-                         (size_t)(nr - t) * width[k] * sizeof(float), st));
+    for (int k = 0; k < np; ++k) {
+      const size_t off = (size_t)first[k] * nr + (size_t)t * width[k];
+      const size_t bytes = (size_t)(nr - t) * width[k] * sizeof(float);
+      if (out_lay) CU(cudaMemsetAsync(out_lay + off, 0, bytes, st));
+      if (x_out != x_in)
+        CU(cudaMemcpyAsync(x_out + off, x_in + off, bytes, cudaMemcpyDeviceToDevice, st));
+    }
   }
   return flux_step_any(s, D, w_lay, x_in, x_out, out_lay, tau, st);
 }
@@ -887,7 +890,7 @@ int ep_adjoint_step(ep_schedule* s, int32_t D, const float* x_lay, const float* 
     return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
   cudaStream_t st = as_stream(stream);
-  if (int rc = ensure_bacc(s, ep::record_floats(D), st)) return rc;
+  if (int rc = ensure_bacc(s, D, st)) return rc;
   return flux_adj_any(s, D, w_lay, x_lay, lam, grad_w_lay, tau, st);
 }
 
@@ -916,8 +919,8 @@ int ep_run(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out,
   if (out) {
     CU(s->ws_out.ensure(lay));
   }
-  if (int rc = ensure_bacc(s, R, st)) return rc;
-  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, x, s->ws_x.as<float>(), st, s->t()));
+  if (int rc = ensure_bacc(s, D, st)) return rc;
+  CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, x, s->ws_x.as<float>(), st, s->t()));
   CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
   if (out) CU(cudaMemsetAsync(s->ws_out.p, 0, lay, st));
   for (int32_t t = 0; t < steps; ++t) {
@@ -969,22 +972,23 @@ int ep_run_adjoint(ep_schedule* s, const float* x0, const float* w, float* lam, 
   CU(s->ws_lam.ensure(lay * sizeof(float)));
   CU(s->ws_w.ensure((size_t)wlen_of(s) * sizeof(float)));
   CU(s->ws_gw.ensure((size_t)wlen_of(s) * sizeof(float)));
-  if (int rc = ensure_bacc(s, R, st)) return rc;
+  if (int rc = ensure_bacc(s, D, st)) return rc;
   float* hist = s->ws_hist.as<float>();
-  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, x0, hist, st, s->t()));
+  CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, x0, hist, st, s->t()));
   CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
   CU(cudaMemsetAsync(s->ws_gw.p, 0, (size_t)wlen_of(s) * sizeof(float), st));
   for (int32_t t = 0; t + 1 < steps; ++t)
     if (int rc = flux_step_any(s, D, s->ws_w.as<float>(), hist + lay * t, hist + lay * (t + 1), nullptr,
                                tau, st))
       return rc;
-  CU(ep::dev::layout_in(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, lam, s->ws_lam.as<float>(), st, s->t()));
+  CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, lam, s->ws_lam.as<float>(), st,
+                            s->t()));
   for (int32_t t = steps - 1; t >= 0; --t)
     if (int rc = flux_adj_any(s, D, s->ws_w.as<float>(), hist + lay * t, s->ws_lam.as<float>(),
                               s->ws_gw.as<float>(), tau, st))
       return rc;
   CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, s->ws_lam.as<float>(), lam, st, s->t()));
-  CU(ep::dev::scatter_add(wmap_of(s), wlen_of(s), s->ws_gw.as<float>(), grad_w, st, s->t()));
+  CU(ep::dev::gather_add(s->d_gslot.as<int32_t>(), h.m, s->ws_gw.as<float>(), grad_w, st, s->t()));
   return EP_OK;
 }
 
@@ -1035,13 +1039,11 @@ int ep_spmv(ep_schedule* s, const float* x_lay, const float* w_lay, float* y_lay
   return spmv_lay(s, x_lay, w_lay, y_lay, as_stream(stream));
 }
 
-int ep_set_pipeline(ep_schedule* s, int32_t stages, int32_t ahead) {
+int ep_set_pipeline(ep_schedule* s, int32_t stages) {
   if (!s) return fail(EP_EINVAL, "null schedule");
   if (stages < 0 || stages == 1 || stages > ep::dev::kMaxStages)
     return fail(EP_EINVAL, "stages = %d (0, or 2..%d)", stages, ep::dev::kMaxStages);
-  if (ahead < 0 || ahead > 64) return fail(EP_EINVAL, "ahead = %d (0..64)", ahead);
   s->stages = stages;
-  s->ahead = ahead;
   return EP_OK;
 }
 

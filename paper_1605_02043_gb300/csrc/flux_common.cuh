@@ -1,0 +1,274 @@
+// flux_common.cuh -- device pieces shared by every flux kernel (sm_103a).
+//
+// The interaction is the particle kernel of the cfd example (Section 1):
+// task e = (u, v) with weight w_e gives f_e = w_e (x_v - x_u) / (1 + |x_v - x_u|^2),
+// out_u += f_e, out_v -= f_e.  The kernels compute it in pull form: the lane
+// that owns position p sums c (x_o - x_p), c = w / (1 + |x_o - x_p|^2), over the
+// slots of p; IEEE subtraction is exactly antisymmetric, so the two endpoints
+// of a task add exactly +f_e and -f_e.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace ep {
+namespace dev {
+
+// The D components of a record live in planes of width 4, 2 and 1
+// (D = 4a + 2b + c).  Plane k starts at component first(k): in a buffer of
+// n records it is the float range [first(k) * n, (first(k) + width(k)) * n).
+template <int D>
+struct Planes {
+  static constexpr int A = D / 4, B = (D % 4) / 2, C1 = D % 2;
+  static constexpr int NP = A + B + C1;
+  __host__ __device__ static constexpr int width(int k) { return k < A ? 4 : (k < A + B ? 2 : 1); }
+  __host__ __device__ static constexpr int first(int k) {
+    return k < A ? 4 * k : (k < A + B ? 4 * A + 2 * (k - A) : 4 * A + 2 * B);
+  }
+};
+
+// Accumulator records of the shared vertices: array of structures with a
+// 16-byte (D <= 4) or 32-byte stride, so one record is one 32-byte sector.
+__host__ __device__ constexpr int acc_stride(int D) { return D <= 4 ? 4 : 8; }
+
+template <int W>
+__device__ __forceinline__ void vld(const float* p, float* v) {
+  if constexpr (W == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  } else if constexpr (W == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x, v[1] = t.y;
+  } else {
+    v[0] = *p;
+  }
+}
+template <int W>
+__device__ __forceinline__ void vld_nc(const float* __restrict__ p, float* v) {
+  if constexpr (W == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+  } else if constexpr (W == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x, v[1] = t.y;
+  } else {
+    v[0] = __ldg(p);
+  }
+}
+template <int W>
+__device__ __forceinline__ void vst(float* p, const float* v) {
+  if constexpr (W == 4)
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else if constexpr (W == 2)
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  else
+    *p = v[0];
+}
+template <int W>
+__device__ __forceinline__ void vred(float* p, const float* v) {
+  if constexpr (W == 4)
+    atomicAdd(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  else if constexpr (W == 2)
+    atomicAdd(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+  else
+    atomicAdd(p, v[0]);
+}
+
+// Record r of a planar buffer of n records <-> registers v[0..D), one vector
+// access per plane.  NC: through the read-only data cache.
+template <int D, bool NC = false, int K = 0>
+__device__ __forceinline__ void rec_load(const float* base, int64_t n, int64_t r, float* v) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    if constexpr (NC)
+      vld_nc<W>(base + F * n + r * W, v + F);
+    else
+      vld<W>(base + F * n + r * W, v + F);
+    rec_load<D, NC, K + 1>(base, n, r, v);
+  }
+}
+template <int D, int K = 0>
+__device__ __forceinline__ void rec_store(float* base, int64_t n, int64_t r, const float* v) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    vst<W>(base + F * n + r * W, v + F);
+    rec_store<D, K + 1>(base, n, r, v);
+  }
+}
+// accumulator record h (array of structures) <-> registers
+template <int D, int K = 0>
+__device__ __forceinline__ void acc_red(float* bacc, int64_t h, const float* v) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    vred<W>(bacc + h * acc_stride(D) + F, v + F);
+    acc_red<D, K + 1>(bacc, h, v);
+  }
+}
+template <int D, int K = 0>
+__device__ __forceinline__ void acc_load(const float* bacc, int64_t h, float* v) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    vld<W>(bacc + h * acc_stride(D) + F, v + F);
+    acc_load<D, K + 1>(bacc, h, v);
+  }
+}
+template <int D, int K = 0>
+__device__ __forceinline__ void acc_zero(float* bacc, int64_t h) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    const float z[4] = {0.f, 0.f, 0.f, 0.f};
+    vst<W>(bacc + h * acc_stride(D) + F, z);
+    acc_zero<D, K + 1>(bacc, h);
+  }
+}
+
+// One slot of the forward pull: acc += w (x_o - x_p) / (1 + |x_o - x_p|^2).
+template <int D, bool NC>
+__device__ __forceinline__ void fwd_entry(const float* xs, int64_t n, int64_t base, uint16_t e, float wt,
+                                          const float* xp, float* acc) {
+  float xo[D];
+  rec_load<D, NC>(xs, n, base + (e & kSlotPos), xo);
+  float q = 0.f;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    xo[c] -= xp[c];
+    q = fmaf(xo[c], xo[c], q);
+  }
+  const float coef = __fdividef(wt, 1.f + q);
+#pragma unroll
+  for (int c = 0; c < D; ++c) acc[c] = fmaf(coef, xo[c], acc[c]);
+}
+
+// Forward pull of one lane over the K columns of its slice.  xs: the state
+// planes (n records, positions offset by `base`), ix / wv: the lane's first
+// slot (the next column is 32 slots further).  Unused slots are skipped.
+template <int D, bool NC>
+__device__ __forceinline__ void fwd_slice(const float* xs, int64_t n, int64_t base,
+                                          const uint16_t* ix, const float* wv, int K,
+                                          const float* xp, float* acc) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) acc[c] = 0.f;
+  int k = 0;
+  for (; k + 1 < K; k += 2) {  // two slots per iteration: their loads are independent
+    uint16_t e0, e1;
+    float w0, w1;
+    if constexpr (NC) {
+      e0 = __ldg(ix + 32 * k), e1 = __ldg(ix + 32 * (k + 1));
+      w0 = __ldg(wv + 32 * k), w1 = __ldg(wv + 32 * (k + 1));
+    } else {
+      e0 = ix[32 * k], e1 = ix[32 * (k + 1)];
+      w0 = wv[32 * k], w1 = wv[32 * (k + 1)];
+    }
+    if (e0 != kSlotNone) fwd_entry<D, NC>(xs, n, base, e0, w0, xp, acc);
+    if (e1 != kSlotNone) fwd_entry<D, NC>(xs, n, base, e1, w1, xp, acc);
+  }
+  if (k < K) {
+    const uint16_t e = NC ? __ldg(ix + 32 * k) : ix[32 * k];
+    const float wt = NC ? __ldg(wv + 32 * k) : wv[32 * k];
+    if (e != kSlotNone) fwd_entry<D, NC>(xs, n, base, e, wt, xp, acc);
+  }
+}
+
+// Adjoint pull of one lane (reverse step at state x, cotangent lam): for the
+// slot to other position o, d = x_o - x_p, g = lam_p - lam_o, q = |d|^2,
+// acc -= w (g / (1 + q) - 2 d (d.g) / (1 + q)^2); the source-side slot of a
+// task adds tau (d.g) / (1 + q) to the task's weight gradient (gslot: that
+// slot's weight-gradient element; one writer per task).
+template <int D>
+__device__ __forceinline__ void adj_slice(const float* xs, const float* ls, int64_t n,
+                                          const uint16_t* ix, const float* wv, int K,
+                                          const float* xp, const float* lp, float* acc,
+                                          float* __restrict__ gslot, float tau) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) acc[c] = 0.f;
+  for (int k = 0; k < K; ++k) {
+    const uint16_t e = ix[32 * k];
+    if (e == kSlotNone) continue;
+    const float we = wv[32 * k];
+    const int o = e & kSlotPos;
+    float xo[D], lo[D];
+    rec_load<D>(xs, n, o, xo);
+    rec_load<D>(ls, n, o, lo);
+    float q = 0.f, dg = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      xo[c] -= xp[c];        // d
+      lo[c] = lp[c] - lo[c];  // g
+      q = fmaf(xo[c], xo[c], q);
+      dg = fmaf(xo[c], lo[c], dg);
+    }
+    const float inv = __fdividef(1.f, 1.f + q);
+    const float two = 2.f * dg * inv * inv;
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[c] -= we * (lo[c] * inv - two * xo[c]);
+    // fire-and-forget reduction: no load on the critical path
+    if (e & kSlotSrc) atomicAdd(gslot + 32 * k, tau * dg * inv);
+  }
+}
+
+// One slice of a forward kernel block staged in shared memory (xs: state
+// planes of npos positions, ix / wv / soff / ssid: the block's slots, slot
+// weights, slice offsets and shared ids): lane `lane` sums the flux at its
+// position and writes back, x_out = x + tau * flux in place for a vertex only
+// this block uses (and out = flux if requested), one vector reduction into the
+// accumulator of a shared vertex.
+template <int D>
+__device__ __forceinline__ void fwd_block_slice(const FluxArgs& a, const FluxDesc& d, const float* xs,
+                                                int npos, const uint16_t* ix, const float* wv,
+                                                const uint16_t* soff, const int32_t* ssid, int sl,
+                                                int lane) {
+  const int p = 32 * sl + lane;
+  const int c0 = soff[sl], K = soff[sl + 1] - c0;
+  float xp[D], acc[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) xp[c] = 0.f;
+  if (p < d.nv) rec_load<D>(xs, npos, p, xp);
+  fwd_slice<D, false>(xs, npos, 0, ix + 32 * c0 + lane, wv + 32 * c0 + lane, K, xp, acc);
+  if (p >= d.nv) return;
+  if (p < d.ni) {
+    float xn[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) xn[c] = fmaf(a.tau, acc[c], xp[c]);
+    rec_store<D>(a.x_out, a.n_rec, (int64_t)d.rec_lo + p, xn);
+    if (a.out) rec_store<D>(a.out, a.n_rec, (int64_t)d.rec_lo + p, acc);
+  } else {
+    acc_red<D>(a.bacc, ssid[p - d.ni], acc);
+  }
+}
+
+// One slice of an adjoint kernel block staged in shared memory (xs, ls: state
+// and cotangent planes): lam_p += tau * acc in place for a vertex only this
+// block uses, one reduction into the accumulator of a shared vertex; gw is the
+// weight gradient in slot layout.
+template <int D>
+__device__ __forceinline__ void adj_block_slice(const FluxArgs& a, const FluxDesc& d, const float* xs,
+                                                const float* ls, int npos, const uint16_t* ix,
+                                                const float* wv, const uint16_t* soff,
+                                                const int32_t* ssid, float* lam, float* gw, int sl,
+                                                int lane) {
+  const int p = 32 * sl + lane;
+  const int c0 = soff[sl], K = soff[sl + 1] - c0;
+  float xp[D], lp[D], acc[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) xp[c] = lp[c] = 0.f;
+  if (p < d.nv) {
+    rec_load<D>(xs, npos, p, xp);
+    rec_load<D>(ls, npos, p, lp);
+  }
+  adj_slice<D>(xs, ls, npos, ix + 32 * c0 + lane, wv + 32 * c0 + lane, K, xp, lp, acc,
+               gw + d.s0 + 32 * c0 + lane, a.tau);
+  if (p >= d.nv) return;
+  if (p < d.ni) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) lp[c] = fmaf(a.tau, acc[c], lp[c]);
+    rec_store<D>(lam, a.n_rec, (int64_t)d.rec_lo + p, lp);
+  } else {
+    acc_red<D>(a.bacc, ssid[p - d.ni], acc);
+  }
+}
+
+}  // namespace dev
+}  // namespace ep

@@ -9,36 +9,42 @@
 
 namespace ep {
 
-// Flux kernels: one descriptor per schedule block.  The block's vertices sit
-// at shared-memory positions
-//   [pi, pi + n_int)   records used by this block only (p_v = 1), contiguous
-//                      from int_lo;
-//   [pb, pb + n_ob)    records first touched by this block and used by later
-//                      blocks too, contiguous from bnd_lo;
-//   [pf, pf + nf)      records owned by earlier blocks, flist[f0 .. f0 + nf);
-// with pi = int_lo mod 4 and pb = bnd_lo mod 4 (mod 4), so that a 16-byte
-// aligned run of records in a state plane maps to a 16-byte aligned run in
-// shared memory.  Positions outside the three runs are unused.  Every
-// position p in [0, np) has the incidence entries inc[i0 + ptr[q0 + p] ..
-// i0 + ptr[q0 + p + 1]): (other position) | (task << 15) | (p is src << 31).
-// The task weights of the block are w_lay[w0 .. w0 + ne).  Every per-block
-// segment (entries, offsets, foreign ids, weights) starts on a 16-byte
-// boundary and is zero-padded to a multiple of 16 bytes, so it can be moved
-// with one bulk copy.
+// Flux kernels: one descriptor per kernel block (a schedule block, or a piece
+// of an oversize one).  The block's vertices V_b sit at positions [0, nv):
+//   [0, ni)    vertices no other kernel block uses (p_v = 1), in-place update;
+//   [ni, nv)   shared vertices (p_v > 1); each kernel block holds its own copy
+//              (replica) of every shared vertex it uses, so position p is always
+//              the state record rec_lo + p and a block's vertex set is one
+//              contiguous run; sid_list[h0 + p - ni] is the shared id that
+//              indexes the accumulators and the copy lists of the fold.
+// Within each class positions are ordered by descending in-block degree.
+// Incidence in sliced-ELL form: slice j holds the positions [32 j, 32 j + 32);
+// its incidence entries occupy K_j = soff[q0 + j + 1] - soff[q0 + j] columns
+// of 32 slots, slot = s0 + 32 * soff[q0 + j] + 32 * column + lane, so that a
+// warp reads one column with one access per array.  A slot holds the other
+// endpoint's position (bits 0-14) and a source flag (bit 15: this position is
+// the task's first endpoint), and the task weight in the same slot of the
+// weight layout; unused slots hold kSlotNone.  Every task has one slot at each
+// endpoint (one for a self loop), so the forward flux is computed from either
+// side without signs (pull form).  Every per-block segment starts on a 16-byte
+// boundary and is padded to a multiple of 16 bytes (one bulk copy each).
 struct FluxDesc {
-  int32_t w0, ne;        // task weights w_lay[w0, w0 + ne)
-  int32_t int_lo, n_int;
-  int32_t bnd_lo, n_ob;
-  int32_t f0, nf;
-  int32_t pi, pb, pf, np;
-  int32_t i0, q0, nent, pad;
+  int32_t rec_lo, nv, ni, nsl;  // record run, positions, interior positions, slices
+  int32_t s0, nslot;            // slots [s0, s0 + nslot), both multiples of 32
+  int32_t h0, q0;               // shared ids sid_list[h0 ..], slice offsets soff[q0 ..]
+  int32_t ne;                   // tasks of the block
+  int32_t pad[7];
 };
 static_assert(sizeof(FluxDesc) == 64, "FluxDesc layout");
 
-// Incidence entry fields
+// Slot fields (flux)
+constexpr uint16_t kSlotPos = 0x7fffu;
+constexpr uint16_t kSlotSrc = 0x8000u;
+constexpr uint16_t kSlotNone = 0xffffu;
+
+// Incidence entry fields (SpMV rows)
 constexpr uint32_t kPosMask = 0x7fffu;
 constexpr int kTaskShift = 15;
-constexpr uint32_t kSrcBit = 0x80000000u;
 
 // SpMV kernels (bipartite): x records are read only, y records accumulate.
 // x positions: [0, n_xo) the run x_lo.., then n_xf ids from xlist[fx0..].
@@ -68,20 +74,22 @@ struct HostSchedule {
   int64_t loads = 0, touched = 0;
   int32_t max_ne = 0;
 
-  // flux layout (non-bipartite)
-  int64_t n_rec = 0;        // records per state plane: nd rounded up to a multiple of 4
-  int64_t n_int = 0;        // records [0, n_int) are single-block vertices
-  int64_t n_bnd = 0;        // records [n_int, n_int + n_bnd) are shared
-  std::vector<int32_t> rec_of;  // data vertex -> record (all nd vertices)
+  // flux layout (non-bipartite), built over the kernel blocks
+  int64_t n_rec = 0;         // records per state plane (multiple of 4)
+  int64_t n_run = 0;         // records [0, n_run) are block runs; untouched vertices follow
+  int64_t n_sh = 0;          // shared vertices (accumulator records)
+  std::vector<int32_t> rec_of;    // data vertex -> its record (a shared vertex: its first copy)
+  std::vector<int32_t> vrec;      // record -> data vertex (-1: padding)
+  std::vector<int32_t> cptr, crec;  // copies of shared vertex s: crec[cptr[s] .. cptr[s+1])
+  std::vector<int32_t> sid_list;  // shared id of every shared position, per block
+  std::vector<uint16_t> sidx;     // slot entries
+  std::vector<uint16_t> soff;     // slice column offsets, per block
+  std::vector<int32_t> gslot;     // task -> its source-side slot
   std::vector<FluxDesc> fdesc;
-  std::vector<int32_t> flist;
-  std::vector<uint32_t> inc;   // incidence entries (flux)
-  std::vector<uint16_t> ptr;   // per-position entry offsets within a block (flux)
-  int32_t max_nv = 0;          // max positions per block
-  int32_t max_nent = 0;        // max incidence entries per block
-  int32_t max_nf = 0;          // max foreign records per block
-  int64_t w_pad = 0;           // length of the padded weight layout
+  int32_t max_nv = 0, max_nslot = 0, max_nsh = 0, max_nsl = 0;
+  int64_t w_pad = 0;           // slots of the weight layout
   std::vector<int32_t> wmap;   // weight slot -> task id (-1 for padding)
+  int32_t max_nent = 0;        // SpMV: max row entries per block
 
   // spmv layout (bipartite): x records 0..n-1, y records 0..n-1
   int64_t ny_int = 0, ny_bnd = 0;

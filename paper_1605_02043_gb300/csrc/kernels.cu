@@ -14,367 +14,164 @@
 #include <mutex>
 #include <unordered_set>
 
+#include "block_distinct.cuh"
+#include "flux_common.cuh"
 #include "kernels.h"
 
 namespace ep {
 namespace dev {
 namespace {
 
-template <int V>
-struct VecOf;
-template <>
-struct VecOf<1> {
-  using T = float;
-};
-template <>
-struct VecOf<2> {
-  using T = float2;
-};
-template <>
-struct VecOf<4> {
-  using T = float4;
-};
-
-// The D components of a record live in planes of width 4, 2 and 1
-// (D = 4a + 2b + c).  Plane k starts at component first(k): in a buffer of
-// n records it is the float range [first(k) * n, (first(k) + width(k)) * n).
-template <int D>
-struct Planes {
-  static constexpr int A = D / 4, B = (D % 4) / 2, C1 = D % 2;
-  static constexpr int NP = A + B + C1;
-  __host__ __device__ static constexpr int width(int k) { return k < A ? 4 : (k < A + B ? 2 : 1); }
-  __host__ __device__ static constexpr int first(int k) {
-    return k < A ? 4 * k : (k < A + B ? 4 * A + 2 * (k - A) : 4 * A + 2 * B);
-  }
-};
-
-template <int W>
-__device__ __forceinline__ void vload(const float* p, float* v) {
-  if constexpr (W == 4) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-  } else if constexpr (W == 2) {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    v[0] = t.x, v[1] = t.y;
-  } else {
-    v[0] = *p;
-  }
-}
-template <int W>
-__device__ __forceinline__ void vload_g(const float* __restrict__ p, float* v) {
-  if constexpr (W == 4) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-  } else if constexpr (W == 2) {
-    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
-    v[0] = t.x, v[1] = t.y;
-  } else {
-    v[0] = __ldg(p);
-  }
-}
-template <int W>
-__device__ __forceinline__ void vstore(float* p, const float* v) {
-  if constexpr (W == 4)
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  else if constexpr (W == 2)
-    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-  else
-    *p = v[0];
-}
-template <int W>
-__device__ __forceinline__ void vred(float* p, const float* v) {
-  if constexpr (W == 4)
-    atomicAdd(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
-  else if constexpr (W == 2)
-    atomicAdd(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
-  else
-    atomicAdd(p, v[0]);
-}
-
-// Record r of a planar buffer of n records <-> registers v[0..D), one vector
-// access per plane (planes unrolled at compile time).
-template <int D, bool GLOBAL, int K = 0>
-__device__ __forceinline__ void rec_load(const float* base, int64_t n, int64_t r, float* v) {
-  if constexpr (K < Planes<D>::NP) {
-    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
-    const float* q = base + F * n + r * W;
-    if constexpr (GLOBAL)
-      vload_g<W>(q, v + F);
-    else
-      vload<W>(q, v + F);
-    rec_load<D, GLOBAL, K + 1>(base, n, r, v);
-  }
-}
-template <int D, int K = 0>
-__device__ __forceinline__ void rec_store(float* base, int64_t n, int64_t r, const float* v) {
-  if constexpr (K < Planes<D>::NP) {
-    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
-    vstore<W>(base + F * n + r * W, v + F);
-    rec_store<D, K + 1>(base, n, r, v);
-  }
-}
-template <int D, int K = 0>
-__device__ __forceinline__ void rec_red(float* base, int64_t n, int64_t r, const float* v) {
-  if constexpr (K < Planes<D>::NP) {
-    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
-    vred<W>(base + F * n + r * W, v + F);
-    rec_red<D, K + 1>(base, n, r, v);
-  }
-}
-
-// record at shared position p of a flux block, -1 for an unused position
-__device__ __forceinline__ int32_t flux_rec(const FluxDesc& d, const int32_t* __restrict__ flist,
-                                            int p) {
-  if (p >= d.pi && p < d.pi + d.n_int) return d.int_lo + (p - d.pi);
-  if (p >= d.pb && p < d.pb + d.n_ob) return d.bnd_lo + (p - d.pb);
-  if (p >= d.pf && p < d.pf + d.nf) return __ldg(flist + d.f0 + (p - d.pf));
-  return -1;
-}
-
-// Shared-memory carve-up of a flux block: planes of npos positions each
-// (npos a multiple of 4 keeps every plane 16-byte aligned), then weights,
-// incidence entries and position offsets.
-struct FluxSmem {
+// Shared-memory carve-up of one kernel block (the stage layout of the
+// pipelined kernels, one stage): state planes, cotangent planes (adjoint),
+// slots, slot weights, shared ids, slice offsets.
+struct BlockSmem {
   float* x;
   float* lam;
+  uint16_t* sidx;
   float* w;
-  uint32_t* ent;
-  uint16_t* ptr;
-  int npos;
+  int32_t* sid;
+  uint16_t* soff;
 };
-template <int D>
-__device__ __forceinline__ FluxSmem flux_smem(const FluxDesc& d, bool with_lam) {
-  extern __shared__ float4 smem4[];
-  FluxSmem s;
-  s.npos = (d.np + 3) & ~3;
-  s.x = reinterpret_cast<float*>(smem4);
-  s.lam = s.x + D * s.npos;
-  s.w = with_lam ? s.lam + D * s.npos : s.lam;
-  s.ent = reinterpret_cast<uint32_t*>(s.w + ((d.ne + 3) & ~3));  // 16-byte aligned pieces
-  s.ptr = reinterpret_cast<uint16_t*>(s.ent + ((d.nent + 3) & ~3));
-  return s;
+__device__ __forceinline__ BlockSmem block_smem(unsigned char* base, const TmaLayout& L) {
+  BlockSmem r;
+  r.x = reinterpret_cast<float*>(base);
+  r.lam = reinterpret_cast<float*>(base + L.off_lam);
+  r.sidx = reinterpret_cast<uint16_t*>(base + L.off_sidx);
+  r.w = reinterpret_cast<float*>(base + L.off_w);
+  r.sid = reinterpret_cast<int32_t*>(base + L.off_sid);
+  r.soff = reinterpret_cast<uint16_t*>(base + L.off_soff);
+  return r;
 }
 
-template <int D>
-__device__ __forceinline__ void stage_block(const FluxDesc& d, const FluxSmem& s,
-                                            const int32_t* __restrict__ flist,
-                                            const uint32_t* __restrict__ inc,
-                                            const uint16_t* __restrict__ ptr,
-                                            const float* __restrict__ w, const float* x, int64_t n_rec,
-                                            const float* lam) {
-  // independent loads first, so no warp waits on a foreign id before issuing
-  // them; the per-block pieces are 16-byte aligned and padded, so they move
-  // as 16-byte vectors
-  const int nw = (d.ne + 3) >> 2, ne4 = (d.nent + 3) >> 2, np8 = (d.np + 1 + 7) >> 3;
-  for (int i = threadIdx.x; i < nw; i += blockDim.x)
-    reinterpret_cast<float4*>(s.w)[i] = __ldg(reinterpret_cast<const float4*>(w + d.w0) + i);
-  for (int i = threadIdx.x; i < ne4; i += blockDim.x)
-    reinterpret_cast<uint4*>(s.ent)[i] = __ldg(reinterpret_cast<const uint4*>(inc + d.i0) + i);
-  for (int i = threadIdx.x; i < np8; i += blockDim.x)
-    reinterpret_cast<uint4*>(s.ptr)[i] = __ldg(reinterpret_cast<const uint4*>(ptr + d.q0) + i);
-  for (int p = threadIdx.x; p < d.np; p += blockDim.x) {
-    const int32_t r = flux_rec(d, flist, p);
-    if (r < 0) continue;
-    float v[D];
-    rec_load<D, true>(x, n_rec, r, v);
-    rec_store<D>(s.x, s.npos, p, v);
-    if (lam) {
-      rec_load<D, false>(lam, n_rec, r, v);
-      rec_store<D>(s.lam, s.npos, p, v);
-    }
+// copy `bytes` (a multiple of 16) as 16-byte vectors, the whole CUDA block
+__device__ __forceinline__ void copy16(void* dst, const void* src, uint32_t bytes) {
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  const uint4* s = reinterpret_cast<const uint4*>(src);
+  for (uint32_t i = threadIdx.x; i < bytes / 16u; i += blockDim.x) d[i] = __ldg(s + i);
+}
+__device__ __forceinline__ uint32_t up16(uint32_t b) { return (b + 15u) & ~15u; }
+
+template <int D, int K = 0>
+__device__ __forceinline__ void copy_run(float* sx, int npos, const float* gx, int64_t n, int lo, int nv) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    copy16(sx + F * npos, gx + F * n + (int64_t)lo * W, up16((uint32_t)nv * W * 4u));
+    copy_run<D, K + 1>(sx, npos, gx, n, lo, nv);
   }
+}
+
+// The same pieces the pipelined kernels bulk-copy, moved by the CUDA block's
+// threads as 16-byte vectors (every piece is 16-byte aligned and padded).
+template <int D>
+__device__ __forceinline__ void stage_block(const FluxDesc& d, const FluxArgs& a, const float* lam,
+                                            const BlockSmem& S, const TmaLayout& L) {
+  copy16(S.sidx, a.sidx + d.s0, (uint32_t)d.nslot * 2u);
+  copy16(S.w, a.w + d.s0, (uint32_t)d.nslot * 4u);
+  copy16(S.soff, a.soff + d.q0, up16((uint32_t)(d.nsl + 1) * 2u));
+  copy16(S.sid, a.sid + d.h0, up16((uint32_t)(d.nv - d.ni) * 4u));
+  copy_run<D>(S.x, L.npos, a.x_in, a.n_rec, d.rec_lo, d.nv);
+  if (lam) copy_run<D>(S.lam, L.npos, lam, a.n_rec, d.rec_lo, d.nv);
 }
 
 // ------------------------------------------------------------- flux forward
 
-// One CUDA block per schedule block.  After staging, the thread of position p
-// sums the flux of every task at p over p's incidence list, reading the other
-// endpoint from shared memory: d = x_o - x_p, f = w d / (1 + |d|^2).  The
-// difference is exactly antisymmetric in IEEE arithmetic, so both endpoints of
-// a task see +f and -f of the same value.
+// One CUDA block per kernel block: stage, then every warp takes slices of 32
+// positions (pull form, flux_common.cuh).  Only the staged copy is read, so
+// the in-place update of the interior records cannot overtake a read.
 template <int D>
-__global__ void __launch_bounds__(1024) flux_fwd_kernel(
-    const FluxDesc* __restrict__ desc, const int32_t* __restrict__ flist,
-    const uint32_t* __restrict__ inc, const uint16_t* __restrict__ ptr, const float* __restrict__ w,
-    const float* x_in, float* x_out, float* __restrict__ bacc, float* __restrict__ out,
-    int64_t n_rec, int64_t n_int, int64_t n_bnd, float tau) {
-  const FluxDesc d = desc[blockIdx.x];
-  const FluxSmem s = flux_smem<D>(d, false);
-  stage_block<D>(d, s, flist, inc, ptr, w, x_in, n_rec, nullptr);
+__global__ void __launch_bounds__(1024) flux_fwd_kernel(const FluxArgs a, TmaLayout L) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const FluxDesc d = a.desc[blockIdx.x];
+  const BlockSmem S = block_smem(smem, L);
+  stage_block<D>(d, a, nullptr, S, L);
   __syncthreads();
-  for (int p = threadIdx.x; p < d.np; p += blockDim.x) {
-    const int k0 = s.ptr[p], k1 = s.ptr[p + 1];
-    if (k0 == k1) continue;  // unused position
-    float xp[D], acc[D];
-    rec_load<D, false>(s.x, s.npos, p, xp);
-#pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] = 0.f;
-    for (int k = k0; k < k1; ++k) {
-      const uint32_t e = s.ent[k];
-      float xo[D];
-      rec_load<D, false>(s.x, s.npos, (int)(e & kPosMask), xo);
-      float dd[D], q = 0.f;
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        dd[c] = xo[c] - xp[c];
-        q = fmaf(dd[c], dd[c], q);
-      }
-      const float coef = __fdividef(s.w[(e >> kTaskShift) & 0xffffu], 1.f + q);
-#pragma unroll
-      for (int c = 0; c < D; ++c) acc[c] = fmaf(coef, dd[c], acc[c]);
-    }
-    const int32_t r = flux_rec(d, flist, p);
-    if (p < d.pi + d.n_int) {
-      float xn[D];
-#pragma unroll
-      for (int c = 0; c < D; ++c) xn[c] = fmaf(tau, acc[c], xp[c]);
-      rec_store<D>(x_out, n_rec, r, xn);
-      if (out) rec_store<D>(out, n_rec, r, acc);
-    } else {
-      rec_red<D>(bacc, n_bnd, r - n_int, acc);
-    }
-  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int sl = warp; sl < d.nsl; sl += nw)
+    fwd_block_slice<D>(a, d, S.x, L.npos, S.sidx, S.w, S.soff, S.sid, sl, lane);
 }
 
 // Read-only-cache variant: the texture-cache kernel of Section 5 (Fig. 7(c)),
 // with the read-only data cache (ld.global.nc) in place of texture binding.
-// No staging: every read of a block's incidence, weights and states goes to
-// global memory through that cache.  Thread t handles positions t, t + T,
-// ..., t + (R-1) T of its block and keeps their sums in registers; writes
-// wait for a block barrier, because interior records are updated in place
-// and other threads of the same block may still be reading them.  Foreign
-// and boundary records are never written by this kernel.
+// No staging: slots, weights and states are read from global memory through
+// that cache.  Warp w takes slices w, w + W, ..., up to R of them, and keeps
+// their sums in registers; writes wait for a block barrier, because interior
+// records are updated in place and other warps may still be reading them.
 template <int D, int R>
-__global__ void __launch_bounds__(1024) flux_fwd_ldg_kernel(
-    const FluxDesc* __restrict__ desc, const int32_t* __restrict__ flist,
-    const uint32_t* __restrict__ inc, const uint16_t* __restrict__ ptr, const float* __restrict__ w,
-    const float* x_in, float* x_out, float* __restrict__ bacc, float* __restrict__ out,
-    int64_t n_rec, int64_t n_int, int64_t n_bnd, float tau) {
-  const FluxDesc d = desc[blockIdx.x];
+__global__ void __launch_bounds__(1024) flux_fwd_ldg_kernel(const FluxArgs a) {
+  const FluxDesc d = a.desc[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   float xp[R][D], acc[R][D];
-  int32_t rec[R];
 #pragma unroll
   for (int i = 0; i < R; ++i) {
-    const int p = (int)threadIdx.x + i * (int)blockDim.x;
-    rec[i] = -1;
+    const int sl = warp + i * nw, p = 32 * sl + lane;
 #pragma unroll
-    for (int c = 0; c < D; ++c) acc[i][c] = 0.f;
-    if (p >= d.np) continue;
-    const int k0 = __ldg(ptr + d.q0 + p), k1 = __ldg(ptr + d.q0 + p + 1);
-    if (k0 == k1) continue;  // unused position
-    rec[i] = flux_rec(d, flist, p);
-    rec_load<D, true>(x_in, n_rec, rec[i], xp[i]);
-    for (int k = k0; k < k1; ++k) {
-      const uint32_t e = __ldg(inc + d.i0 + k);
-      float xo[D];
-      rec_load<D, true>(x_in, n_rec, flux_rec(d, flist, (int)(e & kPosMask)), xo);
-      float dd[D], q = 0.f;
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        dd[c] = xo[c] - xp[i][c];
-        q = fmaf(dd[c], dd[c], q);
-      }
-      const float coef = __fdividef(__ldg(w + d.w0 + ((e >> kTaskShift) & 0xffffu)), 1.f + q);
-#pragma unroll
-      for (int c = 0; c < D; ++c) acc[i][c] = fmaf(coef, dd[c], acc[i][c]);
-    }
+    for (int c = 0; c < D; ++c) xp[i][c] = acc[i][c] = 0.f;
+    if (sl >= d.nsl) continue;
+    const int c0 = __ldg(a.soff + d.q0 + sl), K = __ldg(a.soff + d.q0 + sl + 1) - c0;
+    if (p < d.nv) rec_load<D, true>(a.x_in, a.n_rec, (int64_t)d.rec_lo + p, xp[i]);
+    const int64_t s = (int64_t)d.s0 + 32 * c0 + lane;
+    fwd_slice<D, true>(a.x_in, a.n_rec, d.rec_lo, a.sidx + s, a.w + s, K, xp[i], acc[i]);
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < R; ++i) {
-    const int p = (int)threadIdx.x + i * (int)blockDim.x;
-    if (rec[i] < 0) continue;
-    if (p < d.pi + d.n_int) {
+    const int sl = warp + i * nw, p = 32 * sl + lane;
+    if (sl >= d.nsl || p >= d.nv) continue;
+    if (p < d.ni) {
       float xn[D];
 #pragma unroll
-      for (int c = 0; c < D; ++c) xn[c] = fmaf(tau, acc[i][c], xp[i][c]);
-      rec_store<D>(x_out, n_rec, rec[i], xn);
-      if (out) rec_store<D>(out, n_rec, rec[i], acc[i]);
+      for (int c = 0; c < D; ++c) xn[c] = fmaf(a.tau, acc[i][c], xp[i][c]);
+      rec_store<D>(a.x_out, a.n_rec, (int64_t)d.rec_lo + p, xn);
+      if (a.out) rec_store<D>(a.out, a.n_rec, (int64_t)d.rec_lo + p, acc[i]);
     } else {
-      rec_red<D>(bacc, n_bnd, rec[i] - n_int, acc[i]);
+      acc_red<D>(a.bacc, __ldg(a.sid + d.h0 + p - d.ni), acc[i]);
     }
   }
 }
 
-// shared records: x_out = x_in + tau * acc; out = acc; acc = 0 (plane by plane)
+// The fold of the shared vertices, one thread per shared vertex h: every copy
+// r of h gets x_out[r] = x_in[first copy] + tau * acc[h] (all copies hold the
+// same value), out[r] = acc[h] if out is not null, and acc[h] = 0.
 template <int D>
 __global__ void bnd_update_kernel(const float* x_in, float* x_out, float* __restrict__ bacc,
-                                  float* __restrict__ out, int64_t n_rec, int64_t n_int,
-                                  int64_t n_bnd, float tau) {
+                                  float* __restrict__ out, const int32_t* __restrict__ cptr,
+                                  const int32_t* __restrict__ crec, int64_t n_rec, int64_t n_sh,
+                                  float tau) {
   // launched with programmatic serialisation after the edge kernel: wait for
-  // it (the accumulators and interior records it wrote) before reading
+  // it (the accumulators and records it wrote) before reading
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bnd;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float a[D], x[D];
-    rec_load<D, false>(bacc, n_bnd, i, a);
-    rec_load<D, false>(x_in, n_rec, n_int + i, x);
+  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < n_sh;
+       h += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c0 = cptr[h], c1 = cptr[h + 1];
+    float acc[D], x[D];
+    acc_load<D>(bacc, h, acc);
+    rec_load<D>(x_in, n_rec, crec[c0], x);
 #pragma unroll
-    for (int c = 0; c < D; ++c) x[c] = fmaf(tau, a[c], x[c]);
-    rec_store<D>(x_out, n_rec, n_int + i, x);
-    if (out) rec_store<D>(out, n_rec, n_int + i, a);
-#pragma unroll
-    for (int c = 0; c < D; ++c) a[c] = 0.f;
-    rec_store<D>(bacc, n_bnd, i, a);
+    for (int c = 0; c < D; ++c) x[c] = fmaf(tau, acc[c], x[c]);
+    for (int32_t i = c0; i < c1; ++i) {
+      const int32_t r = crec[i];
+      rec_store<D>(x_out, n_rec, r, x);
+      if (out) rec_store<D>(out, n_rec, r, acc);
+    }
+    acc_zero<D>(bacc, h);
   }
 }
 
 // ------------------------------------------------------------- flux adjoint
 
-// Reverse step: at position p with other endpoint o of a task,
-// d = x_o - x_p, g = lam_p - lam_o, q = |d|^2,
-// contribution to lam_p: -w (g/(1+q) - 2 d (d.g)/(1+q)^2), and the src-side
-// entry adds tau (d.g)/(1+q) to the task's weight gradient.
+// One CUDA block per kernel block, the adjoint step (flux_common.cuh adj_*).
 template <int D>
-__global__ void __launch_bounds__(1024) flux_adj_kernel(
-    const FluxDesc* __restrict__ desc, const int32_t* __restrict__ flist,
-    const uint32_t* __restrict__ inc, const uint16_t* __restrict__ ptr, const float* __restrict__ w,
-    const float* __restrict__ x, float* lam, float* __restrict__ gw, float* __restrict__ bacc,
-    int64_t n_rec, int64_t n_int, int64_t n_bnd, float tau) {
-  const FluxDesc d = desc[blockIdx.x];
-  const FluxSmem s = flux_smem<D>(d, true);
-  stage_block<D>(d, s, flist, inc, ptr, w, x, n_rec, lam);
+__global__ void __launch_bounds__(1024) flux_adj_kernel(const FluxArgs a, float* lam, float* gw,
+                                                        TmaLayout L) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const FluxDesc d = a.desc[blockIdx.x];
+  const BlockSmem S = block_smem(smem, L);
+  stage_block<D>(d, a, lam, S, L);
   __syncthreads();
-  for (int p = threadIdx.x; p < d.np; p += blockDim.x) {
-    const int k0 = s.ptr[p], k1 = s.ptr[p + 1];
-    if (k0 == k1) continue;
-    float xp[D], lp[D], acc[D];
-    rec_load<D, false>(s.x, s.npos, p, xp);
-    rec_load<D, false>(s.lam, s.npos, p, lp);
-#pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] = 0.f;
-    for (int k = k0; k < k1; ++k) {
-      const uint32_t e = s.ent[k];
-      const int o = (int)(e & kPosMask);
-      const int t = (int)((e >> kTaskShift) & 0xffffu);
-      float xo[D], lo[D];
-      rec_load<D, false>(s.x, s.npos, o, xo);
-      rec_load<D, false>(s.lam, s.npos, o, lo);
-      float dd[D], g[D], q = 0.f, dg = 0.f;
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        dd[c] = xo[c] - xp[c];
-        g[c] = lp[c] - lo[c];
-        q = fmaf(dd[c], dd[c], q);
-        dg = fmaf(dd[c], g[c], dg);
-      }
-      const float inv = __fdividef(1.f, 1.f + q);
-      const float we = s.w[t];
-      const float two = 2.f * dg * inv * inv;
-#pragma unroll
-      for (int c = 0; c < D; ++c) acc[c] -= we * (g[c] * inv - two * dd[c]);
-      // one writer per task: a fire-and-forget reduction instead of a load in the loop
-      if (e & kSrcBit) atomicAdd(gw + d.w0 + t, tau * dg * inv);
-    }
-    const int32_t r = flux_rec(d, flist, p);
-    if (p < d.pi + d.n_int) {
-#pragma unroll
-      for (int c = 0; c < D; ++c) lp[c] = fmaf(tau, acc[c], lp[c]);
-      rec_store<D>(lam, n_rec, r, lp);
-    } else {
-      rec_red<D>(bacc, n_bnd, r - n_int, acc);
-    }
-  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int sl = warp; sl < d.nsl; sl += nw)
+    adj_block_slice<D>(a, d, S.x, S.lam, L.npos, S.sidx, S.w, S.soff, S.sid, lam, gw, sl, lane);
 }
 
 // --------------------------------------------------------------------- SpMV
@@ -493,6 +290,22 @@ __global__ void layout_in_kernel(const int32_t* __restrict__ rec_of, int64_t n, 
   }
 }
 
+// flux layout: every record r (block runs with their copies of shared
+// vertices, then the untouched vertices) <- its data vertex vrec[r]; padding
+// records get 0
+template <int D>
+__global__ void layout_in_rec_kernel(const int32_t* __restrict__ vrec, int64_t n, int64_t n_rec,
+                                     const float* __restrict__ x, float* __restrict__ x_lay) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rec;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = __ldg(vrec + r);
+    float t[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) t[c] = v >= 0 ? __ldg(x + (size_t)c * n + v) : 0.f;
+    rec_store<D>(x_lay, n_rec, r, t);
+  }
+}
+
 template <int D>
 __global__ void layout_out_kernel(const int32_t* __restrict__ rec_of, int64_t n, int64_t n_rec,
                                   const float* __restrict__ x_lay, float* __restrict__ x) {
@@ -525,6 +338,13 @@ __global__ void scatter_add_kernel(const int32_t* __restrict__ perm, int64_t m,
   }
 }
 
+__global__ void gather_add_kernel(const int32_t* __restrict__ slot, int64_t m,
+                                  const float* __restrict__ w_lay, float* __restrict__ w) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x)
+    w[t] += __ldg(w_lay + __ldg(slot + t));
+}
+
 // --------------------------------------------------------------------- cost
 
 // One CUDA block per schedule block: bitonic sort of the block's endpoint ids
@@ -534,52 +354,20 @@ __global__ void cost_block_kernel(const int64_t* __restrict__ block_ptr, const i
                                   unsigned long long* __restrict__ loads) {
   extern __shared__ float4 smem4[];
   int32_t* key = reinterpret_cast<int32_t*>(smem4);
-  __shared__ unsigned int warp_sum[32];
   const int64_t e0 = block_ptr[blockIdx.x];
   const int ne = (int)(block_ptr[blockIdx.x + 1] - e0);
   const int nk = 2 * ne;
   for (int i = threadIdx.x; i < P; i += blockDim.x)
     key[i] = i < ne ? eu[e0 + i] : i < nk ? ev[e0 + i - ne] : INT_MAX;
   __syncthreads();
-  for (int k = 2; k <= P; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const int32_t a = key[i], b = key[ixj];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            key[i] = b;
-            key[ixj] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  unsigned int cnt = 0;
-  for (int i = threadIdx.x; i < nk; i += blockDim.x)
-    if (i == 0 || key[i] != key[i - 1]) {
-      ++cnt;
-      touched[key[i]] = 1;
-    }
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = cnt;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    unsigned int v = threadIdx.x < (blockDim.x >> 5) ? warp_sum[threadIdx.x] : 0u;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) atomicAdd(loads, (unsigned long long)v);
-  }
+  block_bitonic_sort(key, P);
+  const unsigned int cnt = count_distinct_sorted(key, nk, [&](int32_t v) { touched[v] = 1; });
+  block_sum_add(cnt, loads);
 }
 
 __global__ void count_flags_kernel(const uint8_t* __restrict__ f, int64_t nd,
                                    unsigned long long* __restrict__ total) {
-  unsigned int cnt = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
-       i += (int64_t)gridDim.x * blockDim.x)
-    cnt += f[i];
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(total, (unsigned long long)cnt);
+  sum_flags(f, nd, total);
 }
 
 int grid_for(int64_t work, int tpb) {
@@ -626,43 +414,47 @@ struct Scope {
   }
 };
 
-size_t flux_smem_bytes(const FluxArgs& a, int D, int copies) {
-  const size_t npos = ((size_t)a.max_np + 3) & ~(size_t)3;
-  const auto up = [](size_t v, size_t m) { return (v + m - 1) / m * m; };
-  return (size_t)copies * D * npos * sizeof(float) + up(a.max_ne, 4) * sizeof(float) +
-         up(a.max_nent, 4) * sizeof(uint32_t) + up((size_t)a.max_np + 1, 8) * sizeof(uint16_t) + 16;
+// PDL launch of the fold (the edge kernel before it may still be draining)
+template <int D>
+cudaError_t fold_launch(const FluxArgs& a, float* x_out, const float* x_in, float* out, cudaStream_t st) {
+  if (a.n_sh <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_for(a.n_sh, 256));
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, bnd_update_kernel<D>, x_in, x_out, a.bacc, out, a.cptr, a.crec,
+                            a.n_rec, a.n_sh, a.tau);
 }
 
 template <int D>
 cudaError_t flux_step_t(const FluxArgs& a, cudaStream_t st) {
-  const size_t smem = flux_smem_bytes(a, D, 1);
+  const TmaLayout L = tma_layout(a, D, false);
+  const size_t smem = (size_t)L.stage_bytes;
   cudaError_t e = allow_smem(flux_fwd_kernel<D>, smem);
   if (e != cudaSuccess) return e;
   if (a.k > 0) {
     Scope sc(a.timer, T_EDGE_FWD, st);
-    flux_fwd_kernel<D><<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w, a.x_in,
-                                                          a.x_out, a.bacc, a.out, a.n_rec, a.n_int,
-                                                          a.n_bnd, a.tau);
+    flux_fwd_kernel<D><<<(unsigned)a.k, a.tpb, smem, st>>>(a, L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (a.n_bnd > 0) {
-    Scope sc(a.timer, T_BND, st);
-    bnd_update_kernel<D><<<grid_for(a.n_bnd, 256), 256, 0, st>>>(a.x_in, a.x_out, a.bacc, a.out,
-                                                                 a.n_rec, a.n_int, a.n_bnd, a.tau);
-  }
-  return cudaGetLastError();
+  Scope sc(a.timer, T_BND, st);
+  return fold_launch<D>(a, a.x_out, a.x_in, a.out, st);
 }
 
 template <int D, int R>
 void flux_ldg_launch(const FluxArgs& a, int threads, cudaStream_t st) {
-  flux_fwd_ldg_kernel<D, R><<<(unsigned)a.k, threads, 0, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w,
-                                                              a.x_in, a.x_out, a.bacc, a.out,
-                                                              a.n_rec, a.n_int, a.n_bnd, a.tau);
+  flux_fwd_ldg_kernel<D, R><<<(unsigned)a.k, threads, 0, st>>>(a);
 }
 
 template <int D>
 cudaError_t flux_step_ldg_t(const FluxArgs& a, cudaStream_t st) {
-  const int R = (a.max_np + 1023) / 1024;  // positions per thread
-  const int threads = std::max(32, (((a.max_np + R - 1) / R) + 31) / 32 * 32);
+  const int R = (a.max_nsl + 31) / 32;  // slices per warp
+  const int threads = 32 * std::max(1, (a.max_nsl + R - 1) / std::max(R, 1));
   if (a.k > 0) {
     Scope sc(a.timer, T_EDGE_FWD, st);
     switch (R) {
@@ -673,32 +465,26 @@ cudaError_t flux_step_ldg_t(const FluxArgs& a, cudaStream_t st) {
       case 4: flux_ldg_launch<D, 4>(a, threads, st); break;
       default: return cudaErrorInvalidValue;
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  if (a.n_bnd > 0) {
-    Scope sc(a.timer, T_BND, st);
-    bnd_update_kernel<D><<<grid_for(a.n_bnd, 256), 256, 0, st>>>(a.x_in, a.x_out, a.bacc, a.out,
-                                                                 a.n_rec, a.n_int, a.n_bnd, a.tau);
-  }
-  return cudaGetLastError();
+  Scope sc(a.timer, T_BND, st);
+  return fold_launch<D>(a, a.x_out, a.x_in, a.out, st);
 }
 
 template <int D>
 cudaError_t flux_adj_t(const FluxArgs& a, float* lam, float* gw, cudaStream_t st) {
-  const size_t smem = flux_smem_bytes(a, D, 2);
+  const TmaLayout L = tma_layout(a, D, true);
+  const size_t smem = (size_t)L.stage_bytes;
   cudaError_t e = allow_smem(flux_adj_kernel<D>, smem);
   if (e != cudaSuccess) return e;
   if (a.k > 0) {
     Scope sc(a.timer, T_EDGE_ADJ, st);
-    flux_adj_kernel<D><<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.flist, a.inc, a.ptr, a.w, a.x_in,
-                                                          lam, gw, a.bacc, a.n_rec, a.n_int, a.n_bnd,
-                                                          a.tau);
+    flux_adj_kernel<D><<<(unsigned)a.k, a.tpb, smem, st>>>(a, lam, gw, L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (a.n_bnd > 0) {
-    Scope sc(a.timer, T_BND, st);
-    bnd_update_kernel<D><<<grid_for(a.n_bnd, 256), 256, 0, st>>>(lam, lam, a.bacc, nullptr, a.n_rec,
-                                                                 a.n_int, a.n_bnd, a.tau);
-  }
-  return cudaGetLastError();
+  Scope sc(a.timer, T_BND, st);
+  return fold_launch<D>(a, lam, lam, nullptr, st);
 }
 
 }  // namespace
@@ -744,28 +530,41 @@ cudaError_t flux_step_ldg(const FluxArgs& a, int D, cudaStream_t st) {
     default: return cudaErrorInvalidValue; \
   }
 
-// shared-vertex fold after a pipelined edge kernel: x_out = x_in + tau*bacc
+// shared-vertex fold after a pipelined edge kernel
 cudaError_t bnd_update(const FluxArgs& a, int D, float* x_out, const float* x_in, float* out,
                        cudaStream_t st) {
-  if (a.n_bnd <= 0) return cudaSuccess;
+  if (a.n_sh <= 0) return cudaSuccess;
   Scope sc(a.timer, T_BND, st);
-  const int g = grid_for(a.n_bnd, 256);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(g);
-  cfg.blockDim = dim3(256);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e = cudaSuccess;
-#define EP_BU(DD)                                                                        \
-  e = cudaLaunchKernelEx(&cfg, bnd_update_kernel<DD>, x_in, x_out, a.bacc, out, a.n_rec, \
-                         a.n_int, a.n_bnd, a.tau)
-  EP_DISPATCH_D(D, EP_BU)
+#define EP_BU(DD) return fold_launch<DD>(a, x_out, x_in, out, st)
+  switch (D) {
+    case 1: EP_BU(1);
+    case 2: EP_BU(2);
+    case 3: EP_BU(3);
+    case 4: EP_BU(4);
+    case 5: EP_BU(5);
+    case 6: EP_BU(6);
+    case 7: EP_BU(7);
+    case 8: EP_BU(8);
+  }
 #undef EP_BU
-  return e != cudaSuccess ? e : cudaGetLastError();
+  return cudaErrorInvalidValue;
+}
+
+TmaLayout tma_layout(const FluxArgs& a, int D, bool adjoint) {
+  auto up = [](int64_t x, int64_t m) { return (x + m - 1) / m * m; };
+  TmaLayout L = {};
+  L.npos = (int)up(a.max_nv, 4);
+  const int64_t xb = (int64_t)D * L.npos * 4;
+  L.off_lam = (int)xb;
+  L.off_sidx = (int)(L.off_lam + (adjoint ? xb : 0));
+  L.off_w = (int)(L.off_sidx + up((int64_t)a.max_nslot * 2, 16));
+  L.off_sid = (int)(L.off_w + (int64_t)a.max_nslot * 4);
+  L.off_soff = (int)(L.off_sid + up((int64_t)a.max_nsh * 4, 16));
+  L.off_desc = (int)(L.off_soff + up((int64_t)(a.max_nsl + 1) * 2, 16));
+  L.stage_bytes = (int)up(L.off_desc + (int64_t)sizeof(FluxDesc), 128);
+  L.stages = 1;
+  L.stall = -1;
+  return L;
 }
 
 cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st) {
@@ -824,7 +623,7 @@ __global__ void __launch_bounds__(1024) spmv_ldg_kernel(
 }
 
 size_t flux_block_smem(const FluxArgs& a, int D, bool adjoint) {
-  return flux_smem_bytes(a, D, adjoint ? 2 : 1);
+  return (size_t)tma_layout(a, D, adjoint).stage_bytes;
 }
 
 size_t spmv_block_smem(const SpmvArgs& a) {
@@ -862,6 +661,16 @@ cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, co
   return cudaGetLastError();
 }
 
+cudaError_t layout_in_rec(const int32_t* vrec, int64_t n, int64_t n_rec, int D, const float* x,
+                          float* x_lay, cudaStream_t st, Timer* t) {
+  Scope sc(t, T_LAYOUT, st);
+  const int g = grid_for(n_rec, 256);
+#define EP_LIN(DD) layout_in_rec_kernel<DD><<<g, 256, 0, st>>>(vrec, n, n_rec, x, x_lay)
+  EP_DISPATCH_D(D, EP_LIN)
+#undef EP_LIN
+  return cudaGetLastError();
+}
+
 cudaError_t layout_out(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x_lay,
                        float* x, cudaStream_t st, Timer* t) {
   Scope sc(t, T_LAYOUT, st);
@@ -883,6 +692,13 @@ cudaError_t scatter_add(const int32_t* perm, int64_t m, const float* w_lay, floa
                         Timer* t) {
   Scope sc(t, T_LAYOUT, st);
   scatter_add_kernel<<<grid_for(m, 256), 256, 0, st>>>(perm, m, w_lay, w);
+  return cudaGetLastError();
+}
+
+cudaError_t gather_add(const int32_t* slot, int64_t m, const float* w_lay, float* w, cudaStream_t st,
+                       Timer* t) {
+  Scope sc(t, T_LAYOUT, st);
+  gather_add_kernel<<<grid_for(m, 256), 256, 0, st>>>(slot, m, w_lay, w);
   return cudaGetLastError();
 }
 

@@ -20,18 +20,20 @@ enum { T_EDGE_FWD = 0, T_BND = 1, T_EDGE_ADJ = 2, T_SPMV = 3, T_LAYOUT = 4, T_CO
 
 struct FluxArgs {
   const FluxDesc* desc;
-  int64_t k;
-  const int32_t* flist;
-  const uint32_t* inc;
-  const uint16_t* ptr;
-  const float* w;      // task weights in schedule order
-  const float* x_in;   // state in schedule layout (planar, n_rec records)
-  float* x_out;        // may equal x_in
-  float* bacc;         // n_bnd records (planar), zero on entry, zero on exit
-  float* out;          // flux in schedule layout or nullptr
-  int64_t n_rec, n_int, n_bnd;
+  int64_t k;             // kernel blocks
+  const uint16_t* sidx;  // slots
+  const uint16_t* soff;  // slice offsets
+  const int32_t* sid;    // shared ids of the shared positions
+  const float* w;        // task weights in slot layout
+  const float* x_in;     // state in schedule layout (planar, n_rec records)
+  float* x_out;          // may equal x_in
+  float* bacc;           // n_sh accumulator records (acc_stride(D) floats each), zero on entry and exit
+  float* out;            // flux in schedule layout or nullptr
+  const int32_t* cptr;   // copies of shared vertex h: crec[cptr[h] .. cptr[h+1])
+  const int32_t* crec;
+  int64_t n_rec, n_sh;
   float tau;
-  int32_t max_np, max_ne, max_nent;
+  int32_t max_nv, max_nslot, max_nsh, max_nsl;
   int tpb;
   Timer* timer;
 };
@@ -70,10 +72,9 @@ struct CostArgs {
 constexpr int kMaxStages = 4;
 struct TmaLayout {
   int npos;  // positions per state plane (multiple of 4)
-  int off_lam, off_w, off_ent, off_ptr, off_flist, off_desc;
+  int off_lam, off_sidx, off_w, off_sid, off_soff, off_desc;
   int stage_bytes;
   int stages;
-  int ahead;  // schedule blocks of look-ahead for L2 prefetch (0: none)
   int stall;  // test hook: leave the stage of this block index unfilled (-1: off)
 };
 struct TmaPlan {
@@ -83,6 +84,8 @@ struct TmaPlan {
   int* err;  // error word (bit 0: a "full" wait expired, bit 1: an "empty" wait expired)
   bool fits = true;  // false: two stages exceed shared memory; use the one-block kernel
 };
+// bytes of one stage (state copies: 1 forward, 2 adjoint) and its layout
+TmaLayout tma_layout(const FluxArgs& a, int D, bool adjoint);
 cudaError_t flux_fwd_tma(const FluxArgs& a, const TmaPlan& P, int D, cudaStream_t st);
 cudaError_t flux_adj_tma(const FluxArgs& a, const TmaPlan& P, int D, float* lam, float* gw,
                          cudaStream_t st);
@@ -91,14 +94,21 @@ const void* flux_tma_kernel_ptr(int D, bool adjoint);
 cudaError_t flux_step(const FluxArgs& a, int D, cudaStream_t st);
 // read-only-cache variant (no staging); needs max_np <= 4096
 cudaError_t flux_step_ldg(const FluxArgs& a, int D, cudaStream_t st);
-cudaError_t bnd_update(const FluxArgs& a, int D, float* x_in_out, const float* x_in, float* out,
+// shared-vertex fold after an edge kernel: every copy of shared vertex h
+// becomes x_in[copy] + tau * bacc[h] in x_out; out (if not null) gets bacc[h];
+// bacc[h] is zeroed
+cudaError_t bnd_update(const FluxArgs& a, int D, float* x_out, const float* x_in, float* out,
                        cudaStream_t st);
 cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st);
 cudaError_t spmv(const SpmvArgs& a, cudaStream_t st);
 // shared memory the one-block kernels stage for the schedule's largest block
 size_t flux_block_smem(const FluxArgs& a, int D, bool adjoint);
 size_t spmv_block_smem(const SpmvArgs& a);
-// n data vertices; state planes of n_rec records
+// flux layout in: record r of x_lay <- x[.][vrec[r]] (0 where vrec[r] < 0), n data
+// vertices, state planes of n_rec records
+cudaError_t layout_in_rec(const int32_t* vrec, int64_t n, int64_t n_rec, int D, const float* x,
+                          float* x_lay, cudaStream_t st, Timer* t);
+// SpMV layout in (one record per vertex): x_lay[rec_of[v]] <- x[v]
 cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x,
                       float* x_lay, cudaStream_t st, Timer* t);
 cudaError_t layout_out(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x_lay,
@@ -107,6 +117,9 @@ cudaError_t gather(const int32_t* perm, int64_t m, const float* w, float* w_lay,
                    Timer* t);
 cudaError_t scatter_add(const int32_t* perm, int64_t m, const float* w_lay, float* w, cudaStream_t st,
                         Timer* t);
+// w[t] += w_lay[slot[t]] for t < m
+cudaError_t gather_add(const int32_t* slot, int64_t m, const float* w_lay, float* w, cudaStream_t st,
+                       Timer* t);
 cudaError_t cost(const CostArgs& a, cudaStream_t st);
 
 }  // namespace dev

@@ -3,12 +3,12 @@
 //
 // ep_cost() keeps its per-vertex "touched" flags in a workspace it allocates
 // with cudaMalloc on first use.  Some callers cannot let a library do that:
-// code running while a stream is being captured into a CUDA graph (cudaMalloc
-// is not allowed there), applications that own all device memory through
-// their own pool and forbid outside allocations, and latency-sensitive loops
-// where an allocation's implicit device synchronisation is not acceptable.
-// ep_cost_noalloc() gives them the same count with the flags in a fixed
-// file-scope device array instead; the caller passes every input and output.
+// applications that hand all device memory to their own pool or framework
+// allocator and forbid allocations behind its back, and latency-bound loops
+// that cannot take the implicit device synchronisation cudaMalloc and
+// cudaFree may cause.  ep_cost_noalloc() gives them the same count with the
+// flags in a fixed file-scope device array instead; the caller passes every
+// input and output.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -16,18 +16,23 @@
 #include <cstdio>
 #include <mutex>
 
+#include "block_distinct.cuh"
 #include "epcache.h"
 
 namespace {
 
-// Scratch flags: one byte per data vertex.  Every GPU that loads this module
-// keeps these EP_NOALLOC_MAX_VERTICES bytes until the process exits; all
-// calls share them (the previous call's flags stay until cleared).
-static __device__ __align__(256) uint8_t g_touched[EP_NOALLOC_MAX_VERTICES];
+// Scratch: one flag byte per data vertex, then a status word.  Every GPU that
+// loads this module keeps these bytes until the process exits; all calls share
+// them (the previous call's contents stay until cleared).
+struct Scratch {
+  uint8_t touched[EP_NOALLOC_MAX_VERTICES];
+  unsigned int status;  // EP_NOALLOC_* bits of the current call
+};
+static __device__ __align__(256) Scratch g_scratch;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-uint8_t* g_addr[kMaxDevices] = {};  // device address of g_touched, per device
+Scratch* g_addr[kMaxDevices] = {};  // device address of g_scratch, per device
 
 thread_local char g_msg[256];
 
@@ -36,60 +41,71 @@ int fail(int code, const char* msg) {
   return code;
 }
 
+// A CUDA runtime call of this entry point failed: record the message and clear
+// the runtime's last-error slot, which that failure has just set, so that the
+// next call on this thread does not see it.
+int fail_cuda(cudaError_t e, const char* what) {
+  snprintf(g_msg, sizeof g_msg, "%s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return EP_ECUDA;
+}
+
 // One CUDA block per schedule block: sort the block's endpoint ids in shared
-// memory (bitonic network over P = power of two >= 2 * tasks), count the
-// distinct ids and flag them in `touched`.
+// memory (bitonic network over P = power of two >= 2 * max_ne), count the
+// distinct ids and flag them.  A block with more than P / 2 tasks (or a
+// negative length) cannot be sorted in the space the caller's max_ne gave:
+// it is not counted and the call's status gets EP_NOALLOC_BAD_BLOCK.  An id
+// outside [0, nd) is counted but not flagged, and sets EP_NOALLOC_BAD_ID.
 __global__ void cost_noalloc_kernel(const int64_t* __restrict__ block_ptr,
                                     const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-                                    int P, int64_t nd, uint8_t* __restrict__ touched,
+                                    int P, int64_t nd, Scratch* __restrict__ s,
                                     unsigned long long* __restrict__ loads) {
   extern __shared__ int32_t keys[];
-  __shared__ unsigned int part[32];
   const int64_t e0 = block_ptr[blockIdx.x];
-  // a block larger than the caller's max_ne is cut to what shared memory holds
-  const int ne = (int)min(block_ptr[blockIdx.x + 1] - e0, (int64_t)(P / 2));
-  const int nk = 2 * ne;
+  const int64_t len = block_ptr[blockIdx.x + 1] - e0;
+  if (len < 0 || len > P / 2) {  // uniform over the CUDA block
+    if (threadIdx.x == 0) atomicOr(&s->status, (unsigned int)EP_NOALLOC_BAD_BLOCK);
+    return;
+  }
+  const int ne = (int)len, nk = 2 * ne;
   for (int i = threadIdx.x; i < P; i += blockDim.x)
     keys[i] = i < ne ? eu[e0 + i] : i < nk ? ev[e0 + i - ne] : INT_MAX;
   __syncthreads();
-  for (int size = 2; size <= P; size <<= 1)
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int j = i ^ stride;
-        if (j > i) {
-          const int32_t a = keys[i], b = keys[j];
-          if ((a > b) == ((i & size) == 0)) {
-            keys[i] = b;
-            keys[j] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  unsigned int distinct = 0;
-  for (int i = threadIdx.x; i < nk; i += blockDim.x)
-    if (i == 0 || keys[i] != keys[i - 1]) {
-      ++distinct;
-      if ((uint64_t)(uint32_t)keys[i] < (uint64_t)nd) touched[keys[i]] = 1;  // ids outside [0, nd) are not flagged
-    }
-  for (int o = 16; o > 0; o >>= 1) distinct += __shfl_down_sync(0xffffffffu, distinct, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = distinct;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    unsigned int v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0u;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) atomicAdd(loads, (unsigned long long)v);
+  ep::dev::block_bitonic_sort(keys, P);
+  bool bad = false;
+  const unsigned int distinct = ep::dev::count_distinct_sorted(keys, nk, [&](int32_t v) {
+    if ((uint64_t)(uint32_t)v < (uint64_t)nd && v >= 0)
+      s->touched[v] = 1;
+    else
+      bad = true;
+  });
+  if (bad) atomicOr(&s->status, (unsigned int)EP_NOALLOC_BAD_ID);
+  ep::dev::block_sum_add(distinct, loads);
+}
+
+__global__ void count_touched_kernel(const Scratch* __restrict__ s, int64_t nd,
+                                     unsigned long long* __restrict__ total) {
+  ep::dev::sum_flags(s->touched, nd, total);
+}
+
+// Last launch of a call: a misused call overwrites both counts.
+__global__ void finish_kernel(const Scratch* __restrict__ s, unsigned long long* __restrict__ counts) {
+  const unsigned int st = s->status;
+  if (st) {
+    counts[0] = EP_NOALLOC_INVALID;
+    counts[1] = st;
   }
 }
 
-__global__ void count_touched_kernel(const uint8_t* __restrict__ touched, int64_t nd,
-                                     unsigned long long* __restrict__ total) {
-  unsigned int c = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nd;
-       i += (int64_t)gridDim.x * blockDim.x)
-    c += touched[i];
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(total, (unsigned long long)c);
+template <typename... KArgs, typename... Args>
+cudaError_t launch(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                   cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 }  // namespace
@@ -112,38 +128,46 @@ extern "C" int ep_cost_noalloc(const int64_t* block_ptr, const int32_t* eu, cons
     cudaGetLastError();
     return fail(EP_ENODEV, "no usable current CUDA device");
   }
-  uint8_t* touched = nullptr;
+  Scratch* scratch = nullptr;
   {
-    // set-up, once per device, with that device current
+    // set-up, once per device, with that device current: the host-side name
+    // g_scratch is not a device address, so look the address up
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_addr[dev]) {
       void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_touched);
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
       if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        return fail(EP_ECUDA, "cudaGetSymbolAddress of the scratch flags failed");
+        if (e != cudaSuccess) return fail_cuda(e, "cudaGetSymbolAddress of the scratch array");
+        return fail(EP_ECUDA, "cudaGetSymbolAddress of the scratch array gave no address");
       }
-      g_addr[dev] = static_cast<uint8_t*>(p);
+      g_addr[dev] = static_cast<Scratch*>(p);
     }
-    touched = g_addr[dev];
+    scratch = g_addr[dev];
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int P = 2;
   while (P < 2 * max_ne) P <<= 1;
   const size_t smem = (size_t)P * sizeof(int32_t);
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(cost_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
-    return fail(EP_ECUDA, "cannot raise the shared-memory limit of the cost kernel");
-  // the flags keep the previous call's contents: clear the part this call uses
-  if (cudaMemsetAsync(touched, 0, (size_t)nd, st) != cudaSuccess ||
-      cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess)
-    return fail(EP_ECUDA, "cudaMemsetAsync failed");
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(cost_noalloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fail_cuda(e, "raising the shared-memory limit of the cost kernel");
+  }
+  // the scratch keeps the previous call's contents: clear the flags this call
+  // uses and the status word
+  e = cudaMemsetAsync(scratch->touched, 0, (size_t)nd, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&scratch->status, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync");
   const int tpb = P >= 1024 ? 1024 : (P < 32 ? 32 : P);
-  cost_noalloc_kernel<<<(unsigned)k, tpb, smem, st>>>(block_ptr, eu, ev, P, nd, touched, counts);
+  e = launch(cost_noalloc_kernel, (unsigned)k, (unsigned)tpb, smem, st, block_ptr, eu, ev, P, nd,
+             scratch, counts);
+  if (e != cudaSuccess) return fail_cuda(e, "launch of the cost kernel");
   int64_t g = (nd + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
-  count_touched_kernel<<<(unsigned)g, 256, 0, st>>>(touched, nd, counts + 1);
-  if (cudaGetLastError() != cudaSuccess) return fail(EP_ECUDA, "kernel launch failed");
+  e = launch(count_touched_kernel, (unsigned)g, 256u, 0, st, (const Scratch*)scratch, nd, counts + 1);
+  if (e != cudaSuccess) return fail_cuda(e, "launch of the flag count");
+  e = launch(finish_kernel, 1u, 1u, 0, st, (const Scratch*)scratch, counts);
+  if (e != cudaSuccess) return fail_cuda(e, "launch of the status check");
   return EP_OK;
 }

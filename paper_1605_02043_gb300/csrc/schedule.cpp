@@ -7,11 +7,13 @@
 //   cpack            ids in order of first appearance over blocks (Section
 //                    4.1, after Ding and Kennedy), untouched vertices last;
 //   cost             loads = sum_b |V_b|, vertex cut = loads - touched (Eq. 1);
-//   kernel layout    the cpack order split into vertices one block uses
-//                    (updated in place by that block) and shared vertices
-//                    (accumulated by atomics), with per-block descriptors,
-//                    incidence lists in shared-memory positions, foreign-id
-//                    lists and padded weights (flux), or row lists (SpMV).
+//   kernel layout    flux: one contiguous record run per kernel block with
+//                    the vertices only that block uses (updated in place)
+//                    followed by its own copies of the shared vertices
+//                    (accumulated by atomics, refreshed by the fold), the
+//                    incidence in sliced-ELL slots with one weight per slot,
+//                    and the copy lists of the shared vertices; SpMV: row
+//                    lists over x records staged by owner and foreign ids.
 #include <algorithm>
 #include <climits>
 #include <thread>
@@ -116,117 +118,122 @@ void class_order(const HostSchedule& s, int64_t b, const std::vector<int32_t>& d
 std::string flux_layout_blocks(HostSchedule& s) {
   std::vector<int32_t> p, owner;
   usage(s, p, owner);
-  s.rec_of.assign(s.nd, -1);
-  s.fdesc.assign(s.k, FluxDesc{});
-  std::vector<int32_t> deg(s.nd, 0), cls;
-  // Every run starts on a multiple of 4 records (gap records stay unused), so
-  // a run is a whole number of 16-byte chunks in every state plane.
-  auto align4 = [](int32_t v) { return (v + 3) & ~3; };
-  int32_t next = 0;
-  for (int64_t b = 0; b < s.k; ++b) {
-    block_degrees(s, b, deg);
-    next = align4(next);
-    s.fdesc[b].int_lo = next;
-    class_order(s, b, deg, [&](int32_t v) { return owner[v] == b && p[v] == 1; }, cls);
-    for (int32_t v : cls) s.rec_of[v] = next++;
-    s.fdesc[b].n_int = next - s.fdesc[b].int_lo;
-    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
-  }
-  next = align4(next);
-  s.n_int = next;
-  for (int64_t b = 0; b < s.k; ++b) {
-    block_degrees(s, b, deg);
-    next = align4(next);
-    s.fdesc[b].bnd_lo = next;
-    class_order(s, b, deg, [&](int32_t v) { return owner[v] == b && p[v] > 1; }, cls);
-    for (int32_t v : cls) s.rec_of[v] = next++;
-    s.fdesc[b].n_ob = next - s.fdesc[b].bnd_lo;
-    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
-  }
-  next = align4(next);
-  s.n_bnd = next - s.n_int;
-  for (int64_t v = 0; v < s.nd; ++v)
-    if (s.rec_of[v] < 0) s.rec_of[v] = next++;
-  s.n_rec = align4(next);  // keeps every plane of a state buffer 16-byte aligned
-  // shared-memory positions, foreign lists and per-position incidence lists
-  s.flist.clear();
-  s.inc.clear();
-  s.ptr.clear();
-  s.max_nv = 0;
-  s.max_nent = 0;
-  s.max_nf = 0;
-  s.wmap.clear();
-  auto pad_to = [](auto& v, size_t mult) {
-    while (v.size() % mult) v.push_back(0);
+  auto align4 = [](int64_t v) { return (v + 3) & ~(int64_t)3; };
+  auto pad_to = [](auto& v, size_t mult, auto fill) {
+    while (v.size() % mult) v.push_back(fill);
   };
-  std::vector<int32_t> pos(s.nd, -1);
-  std::vector<int32_t> cnt;
-  std::vector<uint32_t> ent;
+  // shared ids in order of first appearance over the kernel blocks
+  std::vector<int32_t> sid(s.nd, -1);
+  int64_t n_sh = 0;
+  for (int64_t b = 0; b < s.k; ++b)
+    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
+      const int32_t v = s.vert_list[i];
+      if (p[v] > 1 && sid[v] < 0) sid[v] = (int32_t)n_sh++;
+    }
+  s.n_sh = n_sh;
+  s.fdesc.assign(s.k, FluxDesc{});
+  s.rec_of.assign(s.nd, -1);
+  s.sid_list.clear();
+  s.sidx.clear();
+  s.soff.clear();
+  s.wmap.clear();
+  s.gslot.assign(s.m, -1);
+  s.max_nv = s.max_nslot = s.max_nsh = s.max_nsl = 0;
+  std::vector<std::vector<int32_t>> copies(n_sh);
+  std::vector<int32_t> deg(s.nd, 0), ord, pos(s.nd, -1), cls, col;
+  int64_t next = 0;  // next free record
   for (int64_t b = 0; b < s.k; ++b) {
     FluxDesc& d = s.fdesc[b];
     d.ne = (int32_t)(s.block_ptr[b + 1] - s.block_ptr[b]);
-    while (s.wmap.size() % 4) s.wmap.push_back(-1);
-    d.w0 = (int32_t)s.wmap.size();
-    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) s.wmap.push_back(s.edge_perm[i]);
-    pad_to(s.flist, 4);
-    d.f0 = (int32_t)s.flist.size();
-    // runs are 4-aligned: positions [0, n_int), [pb, pb + n_ob), [pf, pf + nf)
-    // with pb and pf rounded up to multiples of 4 (room for whole 16-byte chunks)
-    d.pi = 0;
-    d.pb = (d.n_int + 3) & ~3;
-    d.pf = d.pb + ((d.n_ob + 3) & ~3);
-    int32_t nf = 0;
     block_degrees(s, b, deg);
-    for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) {
-      const int32_t v = s.vert_list[i];
-      const int32_t r = s.rec_of[v];
-      if (owner[v] == b) pos[v] = r < s.n_int ? d.pi + (r - d.int_lo) : d.pb + (r - d.bnd_lo);
+    // positions: interior vertices, then shared ones, each by descending degree
+    class_order(s, b, deg, [&](int32_t v) { return p[v] == 1; }, ord);
+    d.ni = (int32_t)ord.size();
+    class_order(s, b, deg, [&](int32_t v) { return p[v] > 1; }, cls);
+    ord.insert(ord.end(), cls.begin(), cls.end());
+    d.nv = (int32_t)ord.size();
+    if (d.nv > (int32_t)kSlotPos) return "block touches too many vertices";
+    next = align4(next);
+    d.rec_lo = (int32_t)next;
+    for (int32_t q = 0; q < d.nv; ++q) {
+      const int32_t v = ord[q];
+      pos[v] = q;
+      const int32_t r = (int32_t)(next + q);
+      if (owner[v] == b) s.rec_of[v] = r;  // first copy of a shared vertex
+      if (q >= d.ni) copies[sid[v]].push_back(r);
     }
-    class_order(s, b, deg, [&](int32_t v) { return owner[v] != b; }, cls);
-    for (int32_t v : cls) {
-      pos[v] = d.pf + nf++;
-      s.flist.push_back(s.rec_of[v]);
+    next += d.nv;
+    // shared ids of positions [ni, nv)
+    pad_to(s.sid_list, 4, (int32_t)0);
+    d.h0 = (int32_t)s.sid_list.size();
+    for (int32_t q = d.ni; q < d.nv; ++q) s.sid_list.push_back(sid[ord[q]]);
+    pad_to(s.sid_list, 4, (int32_t)0);
+    // slices of 32 positions; columns = largest degree in the slice
+    d.nsl = (d.nv + 31) / 32;
+    pad_to(s.soff, 8, (uint16_t)0);
+    d.q0 = (int32_t)s.soff.size();
+    int32_t cols = 0;
+    s.soff.push_back(0);
+    for (int32_t j = 0; j < d.nsl; ++j) {
+      int32_t K = 0;
+      for (int32_t q = 32 * j; q < std::min(d.nv, 32 * j + 32); ++q) K = std::max(K, deg[ord[q]]);
+      cols += K;
+      if (cols > 0xffff) return "block has too many incidence entries";
+      s.soff.push_back((uint16_t)cols);
+    }
+    pad_to(s.soff, 8, (uint16_t)0);
+    d.s0 = (int32_t)s.sidx.size();  // a multiple of 32
+    d.nslot = 32 * cols;
+    s.sidx.resize(s.sidx.size() + d.nslot, kSlotNone);
+    s.wmap.resize(s.sidx.size(), -1);
+    // fill: every task at both endpoints in task order (a self loop once);
+    // col[q] counts the entries placed at position q so far
+    col.assign(d.nv, 0);
+    auto slot_of = [&](int32_t q) {
+      const int32_t j = q >> 5;
+      return (int64_t)d.s0 + 32 * ((int64_t)s.soff[d.q0 + j] + col[q]) + (q & 31);
+    };
+    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
+      const int32_t e = s.edge_perm[i];
+      int32_t u, v;
+      task_ends(s, e, u, v);
+      const int32_t pu = pos[u], pv = pos[v];
+      const int64_t su = slot_of(pu);
+      ++col[pu];
+      s.sidx[su] = (uint16_t)((uint32_t)pv | kSlotSrc);
+      s.wmap[su] = e;
+      s.gslot[e] = (int32_t)su;
+      if (v != u) {
+        const int64_t sv = slot_of(pv);
+        ++col[pv];
+        s.sidx[sv] = (uint16_t)pu;
+        s.wmap[sv] = e;
+      }
     }
     for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
-    d.nf = nf;
-    s.max_nf = std::max(s.max_nf, nf);
-    d.np = d.pf + nf;
-    if (d.np > (int32_t)kPosMask + 1) return "block touches too many vertices";
-    s.max_nv = std::max(s.max_nv, d.np);
-    // incidence: every task appears at both endpoints (once for a self loop),
-    // in task order within a position
-    cnt.assign(d.np + 1, 0);
-    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
-      int32_t u, v;
-      task_ends(s, s.edge_perm[i], u, v);
-      ++cnt[pos[u] + 1];
-      if (v != u) ++cnt[pos[v] + 1];
-    }
-    for (int32_t p = 0; p < d.np; ++p) cnt[p + 1] += cnt[p];
-    d.nent = cnt[d.np];
-    pad_to(s.inc, 4);
-    pad_to(s.ptr, 8);
-    d.i0 = (int32_t)s.inc.size();
-    d.q0 = (int32_t)s.ptr.size();
-    for (int32_t p = 0; p <= d.np; ++p) s.ptr.push_back((uint16_t)cnt[p]);
-    pad_to(s.ptr, 8);
-    ent.assign(d.nent, 0);
-    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
-      int32_t u, v;
-      task_ends(s, s.edge_perm[i], u, v);
-      const uint32_t j = (uint32_t)(i - s.block_ptr[b]) << kTaskShift;
-      ent[cnt[pos[u]]++] = (uint32_t)pos[v] | j | kSrcBit;
-      if (v != u) ent[cnt[pos[v]]++] = (uint32_t)pos[u] | j;
-    }
-    s.inc.insert(s.inc.end(), ent.begin(), ent.end());
-    pad_to(s.inc, 4);
-    s.max_nent = std::max(s.max_nent, d.nent);
-    if (s.inc.size() >= (size_t)INT32_MAX || s.ptr.size() >= (size_t)INT32_MAX ||
-        s.wmap.size() >= (size_t)INT32_MAX)
-      return "schedule too large";
+    s.max_nv = std::max(s.max_nv, d.nv);
+    s.max_nslot = std::max(s.max_nslot, d.nslot);
+    s.max_nsh = std::max(s.max_nsh, d.nv - d.ni);
+    s.max_nsl = std::max(s.max_nsl, d.nsl);
+    if (s.sidx.size() >= (size_t)INT32_MAX || next >= INT32_MAX / 2) return "schedule too large";
   }
-  pad_to(s.flist, 4);
-  while (s.wmap.size() % 4) s.wmap.push_back(-1);
+  s.n_run = align4(next);
+  next = s.n_run;
+  for (int64_t v = 0; v < s.nd; ++v)
+    if (s.rec_of[v] < 0) s.rec_of[v] = (int32_t)next++;  // untouched vertices
+  s.n_rec = align4(next);  // keeps every plane of a state buffer 16-byte aligned
+  s.vrec.assign(s.n_rec, -1);
+  for (int64_t v = 0; v < s.nd; ++v) s.vrec[s.rec_of[v]] = (int32_t)v;
+  s.cptr.assign(n_sh + 1, 0);
+  s.crec.clear();
+  s.crec.reserve(s.vert_ptr.back());
+  for (int64_t h = 0; h < n_sh; ++h) {
+    s.crec.insert(s.crec.end(), copies[h].begin(), copies[h].end());
+    s.cptr[h + 1] = (int32_t)s.crec.size();
+  }
+  for (int64_t v = 0; v < s.nd; ++v)  // every copy of a shared vertex maps back to it
+    if (sid[v] >= 0)
+      for (int32_t c = s.cptr[sid[v]]; c < s.cptr[sid[v] + 1]; ++c) s.vrec[s.crec[c]] = (int32_t)v;
   s.w_pad = (int64_t)s.wmap.size();
   return "";
 }

@@ -2,13 +2,17 @@
 
 * 1M-node mesh, C = 512, pipelined kernel with the bench's defaults: schedule,
   vertex lists, relabel and cost bit-exact with the oracle; 10 explicit steps
-  and the 10-step adjoint within 1e-5 relative L2 of the FP64 oracle.
+  and the 10-step adjoint, both through ep_run_adjoint and through the
+  checkpointed autograd function (every 5 steps), against the FP64 oracle.
 * R-MAT scale 20, C = 512, bipartite: full SpMV against the FP64 oracle; the
   schedule is checked through properties that hold at any size (exact block
   sizes, each task once, GPU cost = host cost = loads recomputed from the
   vertex lists); the oracle partition itself is too slow for this size.
-* 512 uneven meshes (batched, one launch): every 64th mesh checked one by one
-  against the oracle after 3 steps.
+* 512 uneven meshes (batched, one launch per kernel) with the autotuner's C
+  and kernel: 20 steps forward and backward (checkpoint every 10) captured in
+  one CUDA graph and replayed; x_T, dL/dx0 and dL/dw of 8 sampled meshes
+  (the smallest, the largest and 6 more) against the oracle mesh by mesh.
+FP32 results: parity.py (relative L2 <= 1e-5 and element-wise bounds).
 """
 import numpy as np
 import pytest
@@ -23,14 +27,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_1605_02043_gb300 as E  # noqa: E402
-
-RTOL = 1e-5
-
-
-def rel_l2(a, b):
-    a = np.asarray(a, np.float64)
-    b = np.asarray(b, np.float64)
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+from parity import check_field, check_state  # noqa: E402
 
 
 def cuda(a):
@@ -45,6 +42,18 @@ def mesh1m():
     return n, src, dst, S
 
 
+@pytest.fixture(scope="module")
+def mesh1m_oracle(mesh1m):
+    n, src, dst, S = mesh1m
+    x0 = W.flux_state(n, 5, 0)
+    w = W.flux_weights(src.size, 0)
+    g = W.loss_weights(n, 5, 1)
+    T, tau = 10, 1e-3
+    xT, fT = O.flux_steps(src, dst, x0, w, T, tau)
+    dx, dw = O.flux_adjoint(src, dst, x0, w, T, tau, g)
+    return dict(x0=x0, w=w, g=g, T=T, tau=tau, xT=xT, fT=fT, dx=dx, dw=dw)
+
+
 def test_mesh1m_schedule_bit_exact(mesh1m):
     n, src, dst, S = mesh1m
     ref = O.ep_schedule(src, dst, n, 512)
@@ -56,26 +65,38 @@ def test_mesh1m_schedule_bit_exact(mesh1m):
     assert ref["loads"] < 0.5 * d["loads"]
 
 
-def test_mesh1m_forward_and_adjoint(mesh1m):
+def test_mesh1m_forward_and_adjoint(mesh1m, mesh1m_oracle):
     n, src, dst, S = mesh1m
+    r = mesh1m_oracle
     S.set_pipeline(3)
     S.set_threads(256)
-    x0 = W.flux_state(n, 5, 0)
-    w = W.flux_weights(src.size, 0)
-    T, tau = 10, 1e-3
-    x = cuda(x0)
+    x = cuda(r["x0"])
     out = torch.zeros_like(x)
-    S.run(x, cuda(w), out, steps=T, tau=tau)
-    xT, fT = O.flux_steps(src, dst, x0, w, T, tau)
-    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
-    assert rel_l2(out.cpu().numpy(), fT) <= RTOL
-    g = W.loss_weights(n, 5, 1)
-    lam = cuda(g)
+    S.run(x, cuda(r["w"]), out, steps=r["T"], tau=r["tau"])
+    check_state(x, r["xT"], r["x0"], r["T"], "x")
+    check_field(out, r["fT"], "out")
+    lam = cuda(r["g"])
     gw = torch.zeros(src.size, device="cuda")
-    S.run_adjoint(cuda(x0), cuda(w), lam, gw, steps=T, tau=tau)
-    dx, dw = O.flux_adjoint(src, dst, x0, w, T, tau, g)
-    assert rel_l2(lam.cpu().numpy(), dx) <= RTOL
-    assert rel_l2(gw.cpu().numpy(), dw) <= RTOL
+    S.run_adjoint(cuda(r["x0"]), cuda(r["w"]), lam, gw, steps=r["T"], tau=r["tau"])
+    check_state(lam, r["dx"], r["g"], r["T"], "dx0")
+    check_field(gw, r["dw"], "dw")
+    assert S.check_errors() == 0
+
+
+def test_mesh1m_autograd_checkpointed(mesh1m, mesh1m_oracle):
+    from paper_1605_02043_gb300.autograd import flux_steps
+
+    n, src, dst, S = mesh1m
+    r = mesh1m_oracle
+    S.set_pipeline(3)
+    S.set_threads(256)
+    x = cuda(r["x0"]).requires_grad_(True)
+    w = cuda(r["w"]).requires_grad_(True)
+    xT = flux_steps(x, w, S, r["T"], r["tau"], 5)
+    xT.backward(cuda(r["g"]))
+    check_state(xT, r["xT"], r["x0"], r["T"], "xT")
+    check_state(x.grad, r["dx"], r["g"], r["T"], "dx0")
+    check_field(w.grad, r["dw"], "dw")
     assert S.check_errors() == 0
 
 
@@ -96,27 +117,53 @@ def test_rmat20_spmv_and_schedule_properties():
     keys = np.unique(np.concatenate([blk * (2 * n) + u, blk * (2 * n) + v]))
     assert keys.size == loads
     x0, w = W.spmv_inputs(n, m, 0)
-    y = torch.empty(n, device="cuda")
-    S.run(cuda(x0), cuda(w), y, kernel=E.SPMV)
-    assert rel_l2(y.cpu().numpy(), O.spmv(rows, cols, x0, w, n)) <= RTOL
+    ref = O.spmv(rows, cols, x0, w, n)
+    for dflt in (False, True):
+        Sx = S if not dflt else E.Schedule.partition(rows, cols, n, 512, bipartite=True, default_order=True)
+        Sx.set_threads(192)
+        y = torch.empty(n, device="cuda")
+        Sx.run(cuda(x0), cuda(w), y, kernel=E.SPMV)
+        check_field(y, ref, f"y default_order={dflt}")
 
 
-def test_batch512_sampled_meshes():
+def test_batch512_cuda_graph_fwd_bwd_autotuned():
     from paper_1605_02043_gb300 import autotune
+    from paper_1605_02043_gb300.autograd import FluxRunner
 
     graphs = W.batch_meshes(512)
-    parts = autotune.partition_many(graphs, 256)
+    parts_by_C = {}
+    tuned = autotune.tune(graphs, D=5, partitions=parts_by_C)
+    parts = parts_by_C.get(tuned["C"]) or autotune.partition_many(graphs, tuned["C"])
     B = E.Schedule.batch(parts)
-    N = sum(g[0] for g in graphs)
+    B.set_pipeline(tuned["stages"])
+    B.set_threads(tuned["threads"])
+    N, M = B.n, B.m
+    T, tau, every = 20, 1e-3, 10
     x0 = W.flux_state(N, 5, 0)
-    w = W.flux_weights(B.m, 0)
-    x = cuda(x0)
-    B.run(x, cuda(w), None, steps=3, tau=1e-3)
-    xg = x.cpu().numpy()
-    offs_n = np.cumsum([0] + [g[0] for g in graphs])
+    w = W.flux_weights(M, 0)
+    g = W.loss_weights(N, 5, 1)
+    R = FluxRunner(B, 5, T, tau, every)
+    R.load(cuda(x0), cuda(w), cuda(g))
+    R.run()  # warm-up outside the capture (allocates the library workspace)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        R.run()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert B.check_errors() == 0
+    xT, dx, dw = (t.cpu().numpy() for t in R.results(cuda(x0), M))
+    offs_n = np.cumsum([0] + [gr[0] for gr in graphs])
     offs_m = np.cumsum([0] + [p.m for p in parts])
-    for i in range(0, 512, 64):
+    sizes = np.array([gr[0] for gr in graphs])
+    pick = {int(np.argmin(sizes)), int(np.argmax(sizes))}
+    pick |= {int(i) for i in np.random.default_rng(3).choice(512, 6, replace=False)}
+    for i in sorted(pick):
         n_i, s_i, d_i = graphs[i]
-        lo, hi = offs_n[i], offs_n[i + 1]
-        xT, _ = O.flux_steps(s_i, d_i, x0[:, lo:hi], w[offs_m[i]:offs_m[i + 1]], 3, 1e-3)
-        assert rel_l2(xg[:, lo:hi], xT) <= RTOL, i
+        lo, hi, mlo, mhi = offs_n[i], offs_n[i + 1], offs_m[i], offs_m[i + 1]
+        xr, _ = O.flux_steps(s_i, d_i, x0[:, lo:hi], w[mlo:mhi], T, tau)
+        dxr, dwr = O.flux_adjoint(s_i, d_i, x0[:, lo:hi], w[mlo:mhi], T, tau, g[:, lo:hi])
+        check_state(xT[:, lo:hi], xr, x0[:, lo:hi], T, f"mesh {i} xT")
+        check_state(dx[:, lo:hi], dxr, g[:, lo:hi], T, f"mesh {i} dx0")
+        check_field(dw[mlo:mhi], dwr, f"mesh {i} dw")

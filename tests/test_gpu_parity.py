@@ -1,7 +1,8 @@
 """CUDA path vs the CPU oracle, through the C ABI (GPU only).
 
 Integers (schedule, vertex lists, relabel, cost) must be bit-exact; FP32
-states and gradients must be within 1e-5 relative L2 of the FP64 oracle.
+states and gradients must be within 1e-5 relative L2 of the FP64 oracle and
+within 1e-4 of the largest reference element in every element (parity.py).
 """
 import numpy as np
 import pytest
@@ -16,14 +17,7 @@ if not torch.cuda.is_available():  # collected on CPU machines, skipped there
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_1605_02043_gb300 as E  # noqa: E402
-
-RTOL = 1e-5
-
-
-def rel_l2(a, b):
-    a = np.asarray(a, np.float64)
-    b = np.asarray(b, np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+from parity import check_field, check_state  # noqa: E402
 
 
 def cuda(a):
@@ -58,10 +52,8 @@ def test_flux_one_step_small_mesh(small_mesh, C, default_order, stages):
     out = torch.zeros_like(x)
     S.run(x, cuda(w), out, steps=1, tau=1e-3)
     x1, f0 = O.flux_steps(src, dst, x0, w, 1, 1e-3)
-    assert rel_l2(out.cpu().numpy(), f0) <= RTOL
-    assert rel_l2(x.cpu().numpy(), x1) <= RTOL
-    # the increment itself, not only the state, must match
-    assert rel_l2(x.cpu().numpy() - x0, x1 - x0) <= 1e-4
+    check_field(out, f0, "out")
+    check_state(x, x1, x0, 1, "x")
     assert S.check_errors() == 0
 
 
@@ -77,8 +69,8 @@ def test_flux_state_widths(small_mesh, D, stages):
     out = torch.zeros_like(x)
     S.run(x, cuda(w), out, steps=3, tau=1e-2)
     xT, fT = O.flux_steps(src, dst, x0, w, 3, 1e-2)
-    assert rel_l2(out.cpu().numpy(), fT) <= RTOL
-    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
+    check_field(out, fT, "out")
+    check_state(x, xT, x0, 3, "x")
 
 
 @pytest.mark.parametrize("C,default_order", [(256, False), (64, False), (1000, False),
@@ -95,16 +87,16 @@ def test_flux_read_only_cache_variant(small_mesh, C, default_order, D):
     out = torch.zeros_like(x)
     S.run(x, cuda(w), out, steps=3, tau=1e-2)
     xT, fT = O.flux_steps(src, dst, x0, w, 3, 1e-2)
-    assert rel_l2(out.cpu().numpy(), fT) <= RTOL
-    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
+    check_field(out, fT, "out")
+    check_state(x, xT, x0, 3, "x")
     # the adjoint keeps its staged kernel under this mode
     g = W.loss_weights(n, D, 1)
     lam = cuda(g)
     gw = torch.zeros(src.size, device="cuda")
     S.run_adjoint(cuda(x0), cuda(w), lam, gw, steps=2, tau=1e-2)
     dx, dw = O.flux_adjoint(src, dst, x0, w, 2, 1e-2, g)
-    assert rel_l2(lam.cpu().numpy(), dx) <= RTOL
-    assert rel_l2(gw.cpu().numpy(), dw) <= RTOL
+    check_state(lam, dx, g, 2, "dx0")
+    check_field(gw, dw, "dw")
 
 
 def test_flux_tau_zero_is_pure_flux(small_mesh):
@@ -116,7 +108,7 @@ def test_flux_tau_zero_is_pure_flux(small_mesh):
     out = torch.zeros_like(x)
     S.run(x, cuda(w), out, steps=2, tau=0.0)
     assert torch.equal(x.cpu(), torch.from_numpy(x0))
-    assert rel_l2(out.cpu().numpy(), O.flux(src, dst, x0, w)) <= RTOL
+    check_field(out, O.flux(src, dst, x0, w), "out")
 
 
 def test_flux_edge_cases():
@@ -138,8 +130,8 @@ def test_flux_edge_cases():
             x = cuda(x0)
             out = torch.zeros_like(x)
             S.run(x, cuda(w), out, steps=2, tau=1e-2)
-            assert rel_l2(out.cpu().numpy(), f0) <= RTOL, (C, stages)
-            assert rel_l2(x.cpu().numpy(), x1) <= RTOL, (C, stages)
+            check_field(out, f0, f"out C={C} stages={stages}")
+            check_state(x, x1, x0, 2, f"x C={C} stages={stages}")
             assert np.array_equal(x.cpu().numpy()[:, 200:], x0[:, 200:])  # untouched
             assert S.check_errors() == 0
 
@@ -155,13 +147,14 @@ def test_large_blocks():
     x = cuda(x0)
     S.run(x, cuda(w), None, steps=2, tau=1e-3)
     xT, _ = O.flux_steps(src, dst, x0, w, 2, 1e-3)
-    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
+    check_state(x, xT, x0, 2, "x")
     g = W.loss_weights(n, 5, 1)
     lam = cuda(g)
     gw = torch.zeros(src.size, device="cuda")
     S.run_adjoint(cuda(x0), cuda(w), lam, gw, steps=1, tau=1e-3)
     dx, dw = O.flux_adjoint(src, dst, x0, w, 1, 1e-3, g)
-    assert rel_l2(lam.cpu().numpy(), dx) <= RTOL and rel_l2(gw.cpu().numpy(), dw) <= RTOL
+    check_state(lam, dx, g, 1, "dx0")
+    check_field(gw, dw, "dw")
     big = E.Schedule.partition(src, dst, n, 16384)
     check_schedule_matches_oracle(big, O.ep_schedule(src, dst, n, 16384))
     for stages in (3, 0):
@@ -207,8 +200,8 @@ def test_step_api_matches_run(small_mesh):
     out = torch.zeros_like(x)
     S.layout_out(ol, out)
     xT, fT = O.flux_steps(src, dst, x0, w, 2, 1e-3)
-    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
-    assert rel_l2(out.cpu().numpy(), fT) <= RTOL
+    check_state(x, xT, x0, 2, "x")
+    check_field(out, fT, "out")
 
 
 @pytest.mark.parametrize("C,default_order", [(512, False), (512, True), (64, False), (2048, True)])
@@ -220,7 +213,7 @@ def test_spmv_read_only_cache(C, default_order):
     S.set_cache(E.CACHE_L1)
     y = torch.full((n,), 3.0, device="cuda")
     S.run(cuda(x0), cuda(w), y, kernel=E.SPMV)
-    assert rel_l2(y.cpu().numpy(), O.spmv(r, c, x0, w, n)) <= RTOL
+    check_field(y, O.spmv(r, c, x0, w, n), "y")
 
 
 @pytest.mark.parametrize("C,default_order,threads", [(512, False, 192), (512, True, 192), (64, False, 64),
@@ -237,7 +230,7 @@ def test_spmv_rmat(C, default_order, threads):
     y = torch.full((n,), 3.0, device="cuda")
     S.run(cuda(x0), cuda(w), y, kernel=E.SPMV)
     ref = O.spmv(r, c, x0, w, n)
-    assert rel_l2(y.cpu().numpy(), ref) <= RTOL
+    check_field(y, ref, "y")
     # rows without tasks are zero
     empty = np.setdiff1d(np.arange(n), r)
     assert torch.all(y[torch.from_numpy(empty).cuda()] == 0)
@@ -250,7 +243,7 @@ def test_spmv_rmat(C, default_order, threads):
     S.spmv(xl, wl, yl)
     y2 = torch.empty(n, device="cuda")
     S.spmv_y_out(yl, y2)
-    assert rel_l2(y2.cpu().numpy(), ref) <= RTOL
+    check_field(y2, ref, "y (layout entry points)")
 
 
 @pytest.mark.parametrize("stages", [0, 3])
@@ -266,10 +259,8 @@ def test_adjoint_matches_oracle(small_mesh, stages):
     lam = cuda(g)
     gw = torch.zeros(src.size, device="cuda")
     S.run_adjoint(cuda(x0), cuda(w), lam, gw, steps=T, tau=tau)
-    assert rel_l2(lam.cpu().numpy(), dx_ref) <= RTOL
-    assert rel_l2(gw.cpu().numpy(), dw_ref) <= RTOL
-    # the part of dL/dx0 that the flux adds on top of g
-    assert rel_l2(lam.cpu().numpy() - g, dx_ref - g) <= 1e-4
+    check_state(lam, dx_ref, g, T, "dx0")
+    check_field(gw, dw_ref, "dw")
 
 
 def test_run_host_matches_device(small_mesh):
@@ -282,8 +273,8 @@ def test_run_host_matches_device(small_mesh):
     oh = torch.zeros_like(xh).pin_memory()
     S.run_host(xh, wh, oh, steps=4, tau=1e-3, D=5)
     xT, fT = O.flux_steps(src, dst, x0, w, 4, 1e-3)
-    assert rel_l2(xh.numpy(), xT) <= RTOL
-    assert rel_l2(oh.numpy(), fT) <= RTOL
+    check_state(xh, xT, x0, 4, "x")
+    check_field(oh, fT, "out")
 
 
 def test_batch_schedule(small_mesh):
@@ -302,7 +293,7 @@ def test_batch_schedule(small_mesh):
     x = cuda(x0)
     B.run(x, cuda(w), None, steps=3, tau=1e-3)
     xT, _ = O.flux_steps(src, dst, x0, w, 3, 1e-3)
-    assert rel_l2(x.cpu().numpy(), xT) <= RTOL
+    check_state(x, xT, x0, 3, "x")
 
 
 def test_errors_are_reported(small_mesh):
@@ -340,9 +331,9 @@ def test_autograd_function_matches_oracle(small_mesh):
         wt = cuda(w).requires_grad_(True)
         xT = flux_steps(x, wt, S, T, tau, every)
         xT.backward(cuda(g))
-        assert rel_l2(xT.detach().cpu().numpy(), xT_ref) <= RTOL
-        assert rel_l2(x.grad.cpu().numpy(), dx_ref) <= RTOL, every
-        assert rel_l2(wt.grad.cpu().numpy(), dw_ref) <= RTOL, every
+        check_state(xT, xT_ref, x0, T, f"xT every={every}")
+        check_state(x.grad, dx_ref, g, T, f"dx0 every={every}")
+        check_field(wt.grad, dw_ref, f"dw every={every}")
 
 
 def test_runner_in_cuda_graph_matches_eager_and_oracle():
@@ -372,9 +363,115 @@ def test_runner_in_cuda_graph_matches_eager_and_oracle():
         graph.replay()
     torch.cuda.synchronize()
     xT_g, dx_g, dw_g = R.results(cuda(x0), B.m)
-    assert rel_l2(xT_g.cpu().numpy(), xT_e.cpu().numpy()) <= RTOL
-    assert rel_l2(dx_g.cpu().numpy(), dx_e.cpu().numpy()) <= RTOL
+    check_field(xT_g, xT_e.cpu().numpy(), "xT graph vs eager")
+    check_field(dx_g, dx_e.cpu().numpy(), "dx0 graph vs eager")
+    xT_ref, _ = O.flux_steps(src, dst, x0, w, T, tau)
     dx_ref, dw_ref = O.flux_adjoint(src, dst, x0, w, T, tau, g)
-    assert rel_l2(dx_g.cpu().numpy(), dx_ref) <= RTOL
-    assert rel_l2(dw_g.cpu().numpy(), dw_ref) <= RTOL
+    check_state(xT_g, xT_ref, x0, T, "xT")
+    check_state(dx_g, dx_ref, g, T, "dx0")
+    check_field(dw_g, dw_ref, "dw")
     assert B.check_errors() == 0
+
+
+# ------------------------------------------------------------ pre-screen presets
+
+def _flux_fwd_adj_vs_oracle(S, src, dst, n, label, stages_list=(0, 3)):
+    """Three forward steps and a two-step adjoint of schedule S against the oracle."""
+    x0 = W.flux_state(n, 5, 11)
+    w = W.flux_weights(src.size, 11)
+    g = W.loss_weights(n, 5, 3)
+    for stages in stages_list:
+        S.set_pipeline(stages)
+        x = cuda(x0)
+        out = torch.zeros_like(x)
+        S.run(x, cuda(w), out, steps=3, tau=1e-2)
+        xT, fT = O.flux_steps(src, dst, x0, w, 3, 1e-2)
+        check_field(out, fT, f"{label} out stages={stages}")
+        check_state(x, xT, x0, 3, f"{label} x stages={stages}")
+        lam = cuda(g)
+        gw = torch.zeros(src.size, device="cuda")
+        S.run_adjoint(cuda(x0), cuda(w), lam, gw, steps=2, tau=1e-2)
+        dx, dw = O.flux_adjoint(src, dst, x0, w, 2, 1e-2, g)
+        check_state(lam, dx, g, 2, f"{label} dx0 stages={stages}")
+        check_field(gw, dw, f"{label} dw stages={stages}")
+        assert S.check_errors() == 0
+
+
+@pytest.mark.parametrize("m,C", [(5000, 256), (777, 64), (40, 7)])
+def test_path_preset_runs_through_flux_kernels(m, C):
+    from test_prescreen import path_graph
+
+    src, dst, n = path_graph(m, 5)
+    S = E.Schedule.partition(src, dst, n, C, prescreen=True)
+    assert S.origin == "path"
+    ref = O.ep_schedule(src, dst, n, C, prescreen=True)
+    check_schedule_matches_oracle(S, ref)
+    assert ref["loads"] == m + -(-m // C)  # the preset's closed form, m + k
+    _flux_fwd_adj_vs_oracle(S, src, dst, n, "path")
+
+
+def test_star_and_low_reuse_presets_run_through_flux_kernels():
+    from test_prescreen import star_graph
+
+    # a star: every block shares the centre (one copy per block, folded each step)
+    src, dst, n = star_graph(3000, 2)
+    S = E.Schedule.partition(src, dst, n, 256, prescreen=True)
+    assert S.origin == "star"
+    check_schedule_matches_oracle(S, O.ep_schedule(src, dst, n, 256, prescreen=True))
+    _flux_fwd_adj_vs_oracle(S, src, dst, n, "star")
+    # a matching (every vertex used once): little reuse, the default order is kept
+    rng = np.random.default_rng(8)
+    ids = rng.permutation(4000).astype(np.int32)
+    src, dst, n = ids[0::2], ids[1::2], 4000
+    S = E.Schedule.partition(src, dst, n, 128, prescreen=True)
+    assert S.origin == "low_reuse"
+    check_schedule_matches_oracle(S, O.ep_schedule(src, dst, n, 128, prescreen=True))
+    _flux_fwd_adj_vs_oracle(S, src, dst, n, "low_reuse")
+
+
+@pytest.mark.parametrize("shape", ["path", "star"])
+def test_presets_run_through_spmv_kernel(shape):
+    from test_prescreen import path_graph
+
+    if shape == "path":  # a bidiagonal-like matrix: its bipartite graph is one path
+        rows, cols, n = path_graph(3001, 4, bipartite=True)
+    else:  # one dense row: every task uses row 7 and a column of its own
+        n = 2500
+        cols = np.random.default_rng(5).permutation(n).astype(np.int32)
+        rows = np.full(n, 7, np.int32)
+    S = E.Schedule.partition(rows, cols, n, 128, bipartite=True, prescreen=True)
+    assert S.origin == shape
+    check_schedule_matches_oracle(S, O.ep_schedule(rows, cols, n, 128, bipartite=True, prescreen=True))
+    x0, w = W.spmv_inputs(n, rows.size, 2)
+    for cache in (E.CACHE_SMEM, E.CACHE_L1):
+        S.set_cache(cache)
+        y = torch.full((n,), 3.0, device="cuda")
+        S.run(cuda(x0), cuda(w), y, kernel=E.SPMV)
+        check_field(y, O.spmv(rows, cols, x0, w, n), f"{shape} y cache={cache}")
+
+
+# ------------------------------------------------------------------- autotuner
+
+def test_autotuner_pick_runs_against_oracle():
+    from paper_1605_02043_gb300 import autotune
+
+    sizes = (900, 1500, 2200, 3100, 1200, 4000, 2600, 1800)
+    graphs = [(nn, *W.knn_mesh(nn, 4, 70 + i)) for i, nn in enumerate(sizes)]
+    Cs = (128, 256)
+    kernels = ((3, 128), (2, 256), (0, 128))
+    tuned = autotune.tune(graphs, D=5, Cs=Cs, kernels=kernels, sample=5, reps=3, cache=None,
+                          confirm=2)
+    assert len(tuned["table"]) == len(Cs) * len(kernels)
+    assert tuned["C"] in Cs and (tuned["stages"], tuned["threads"]) in kernels
+    # the pick is the fastest row of its own confirmation
+    conf = tuned["confirmed"]
+    best = min(conf, key=lambda r: r["ms"])
+    assert (best["C"], best["stages"], best["threads"]) == (tuned["C"], tuned["stages"], tuned["threads"])
+    parts = autotune.partition_many(graphs, tuned["C"])
+    B = E.Schedule.batch(parts)
+    B.set_pipeline(tuned["stages"])
+    B.set_threads(tuned["threads"])
+    offs = np.cumsum((0,) + sizes[:-1])
+    src = np.concatenate([g[1] + o for g, o in zip(graphs, offs)]).astype(np.int32)
+    dst = np.concatenate([g[2] + o for g, o in zip(graphs, offs)]).astype(np.int32)
+    _flux_fwd_adj_vs_oracle(B, src, dst, sum(sizes), "autotuned batch", (tuned["stages"],))
