@@ -352,6 +352,18 @@ int ep_set_threads(ep_schedule *s, int32_t threads);
 int ep_set_pipeline(ep_schedule *s, int32_t stages);
 
 /*
+ * No counterpart in the paper (instrumentation): the launch plan the
+ * pipelined kernels use for state width D (adjoint != 0: the adjoint kernel)
+ * on the current device: *grid CUDA blocks (*per_sm per SM) of *threads
+ * threads, *stages shared-memory stages of *stage_bytes bytes each.
+ * *stages = 0 when the schedule's blocks do not fit two stages (the one-block
+ * kernel runs instead) or when ep_set_pipeline chose 0.  Any output may be
+ * NULL.  Needs a device (EP_ENODEV otherwise).
+ */
+int ep_pipeline_info(ep_schedule *s, int32_t D, int32_t adjoint, int32_t *grid, int32_t *per_sm,
+                     int32_t *threads, int32_t *stages, int32_t *stage_bytes);
+
+/*
  * Reads and clears the error word of the pipelined kernels (synchronises
  * `stream`): every wait inside them is bounded, and an expired wait sets a
  * bit here instead of hanging (bit 0: waiting for data, bit 1: waiting for a

@@ -219,6 +219,12 @@ class Schedule:
         with that many shared-memory stages."""
         check(lib().ep_set_pipeline(self._h, stages))
 
+    def pipeline_info(self, D: int = 5, adjoint: bool = False) -> dict:
+        """Launch plan of the pipelined kernels (ep_pipeline_info)."""
+        v = [ctypes.c_int32() for _ in range(5)]
+        check(lib().ep_pipeline_info(self._h, D, int(adjoint), *(ctypes.byref(x) for x in v)))
+        return dict(zip(("grid", "per_sm", "threads", "stages", "stage_bytes"), (x.value for x in v)))
+
     def check_errors(self, stream=None) -> int:
         """Error word of the pipelined kernels (raises EpError when non-zero)."""
         code = ctypes.c_int32()

@@ -139,7 +139,7 @@ struct ep_schedule {
   // device copy of the schedule
   DBuf d_desc, d_flist, d_ylist, d_inc, d_ptr, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
       d_ev;
-  DBuf d_sidx, d_soff, d_sid, d_cptr, d_crec, d_vrec, d_gslot;  // flux layout
+  DBuf d_sidx, d_soff, d_sid, d_vrec, d_gslot, d_frec, d_fsid;  // flux layout
   // workspace
   DBuf ws_x, ws_out, ws_w, ws_bacc, ws_lam, ws_gw, ws_hist, ws_flags, ws_cnt;
   DBuf ws_hx, ws_hw, ws_hout;
@@ -148,7 +148,8 @@ struct ep_schedule {
   int stages = 3;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
   int stall = -1;  // test hook of the bounded waits (ep_debug_stall)
   int cache = EP_CACHE_SMEM;  // forward flux kernel family (ep_set_cache)
-  DBuf ws_ctl;     // [0] block counter, [1] error word
+  // [0] accumulator phase, [1] fold blocks finished, [2] error word
+  DBuf ws_ctl;
   int sm_count = 0;
   // launch plans of the pipelined kernels, cached per (D, adjoint) so that
   // steps inside a stream capture only enqueue work
@@ -159,6 +160,8 @@ struct ep_schedule {
 namespace {
 
 bool bipartite(const ep_schedule* s) { return (s->h.flags & EP_BIPARTITE) != 0; }
+
+constexpr int kCtlWords = 4;
 
 #define CU(call)                                                                          \
   do {                                                                                    \
@@ -208,9 +211,9 @@ int ensure_device(ep_schedule* s) {
     CU(upload(s->d_sidx, h.sidx));
     CU(upload(s->d_soff, h.soff));
     CU(upload(s->d_sid, h.sid_list));
-    CU(upload(s->d_cptr, h.cptr));
-    CU(upload(s->d_crec, h.crec));
     CU(upload(s->d_vrec, h.vrec));
+    CU(upload(s->d_frec, h.fold_rec));
+    CU(upload(s->d_fsid, h.fold_sid));
     CU(upload(s->d_gslot, h.gslot));
     CU(upload(s->d_wmap, h.wmap));
     CU(upload(s->d_rec, h.rec_of));
@@ -238,9 +241,11 @@ ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, f
   a.x_in = x_in;
   a.x_out = x_out;
   a.bacc = s->ws_bacc.as<float>();
+  a.phase = s->ws_ctl.as<int>();
   a.out = out;
-  a.cptr = s->d_cptr.as<int32_t>();
-  a.crec = s->d_crec.as<int32_t>();
+  a.fold_rec = s->d_frec.as<int32_t>();
+  a.fold_sid = s->d_fsid.as<int32_t>();
+  a.n_copies = (int64_t)s->h.fold_rec.size();
   a.n_rec = s->h.n_rec;
   a.n_sh = s->h.n_sh;
   a.tau = tau;
@@ -299,24 +304,32 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
   int per_sm = 0;
   CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P.threads, P.smem));
   if (per_sm < 1) return fail(EP_EINVAL, "pipelined kernel does not fit on an SM");
+  P.per_sm = per_sm;
   P.grid = (int)std::min<int64_t>((int64_t)h.fdesc.size(), (int64_t)per_sm * s->sm_count);
   if (!s->ws_ctl.p) {
-    CU(s->ws_ctl.ensure(2 * sizeof(int)));
-    CU(cudaMemset(s->ws_ctl.p, 0, 2 * sizeof(int)));
+    CU(s->ws_ctl.ensure(kCtlWords * sizeof(int)));
+    CU(cudaMemset(s->ws_ctl.p, 0, kCtlWords * sizeof(int)));
   }
-  P.err = s->ws_ctl.as<int>() + 1;
+  P.err = s->ws_ctl.as<int>() + 2;
   return EP_OK;
 }
 
-// boundary accumulators: allocated, zero
+// accumulators of the shared vertices (two buffers, see acc_buffer) and the
+// control words: allocated; both buffers zero and the phase reset after an
+// allocation or an interrupted launch
 int ensure_bacc(ep_schedule* s, int32_t D, cudaStream_t st) {
-  const size_t bytes = (size_t)s->h.n_sh * ep::dev::acc_stride(D) * sizeof(float);
+  const size_t bytes = 2 * (size_t)s->h.n_sh * ep::dev::acc_stride(D) * sizeof(float);
   if (s->ws_bacc.bytes < bytes || !s->ws_bacc.p) {
     CU(s->ws_bacc.ensure(bytes));
     s->bacc_dirty = true;
   }
-  if (s->bacc_dirty) {
+  if (!s->ws_ctl.p) {
+    CU(s->ws_ctl.ensure(kCtlWords * sizeof(int)));
+    CU(cudaMemsetAsync(s->ws_ctl.p, 0, kCtlWords * sizeof(int), st));
+  }
+  if (s->bacc_dirty) {  // every control word but the error word
     CU(cudaMemsetAsync(s->ws_bacc.p, 0, s->ws_bacc.bytes, st));
+    CU(cudaMemsetAsync(s->ws_ctl.p, 0, 2 * sizeof(int), st));
     s->bacc_dirty = false;
   }
   return EP_OK;
@@ -1047,20 +1060,39 @@ int ep_set_pipeline(ep_schedule* s, int32_t stages) {
   return EP_OK;
 }
 
+int ep_pipeline_info(ep_schedule* s, int32_t D, int32_t adjoint, int32_t* grid, int32_t* per_sm,
+                     int32_t* threads, int32_t* stages, int32_t* stage_bytes) {
+  g_error.clear();
+  if (int rc = check_flux(s, D)) return rc;
+  if (int rc = ensure_device(s)) return rc;
+  int32_t g = 0, p = 0, t = 0, st = 0, sb = 0;
+  if (s->stages != 0) {
+    ep::dev::TmaPlan P;
+    if (int rc = tma_plan(s, D, adjoint != 0, P)) return rc;
+    if (P.fits) g = P.grid, p = P.per_sm, t = P.threads, st = P.L.stages, sb = P.L.stage_bytes;
+  }
+  if (grid) *grid = g;
+  if (per_sm) *per_sm = p;
+  if (threads) *threads = t;
+  if (stages) *stages = st;
+  if (stage_bytes) *stage_bytes = sb;
+  return EP_OK;
+}
+
 int ep_check_errors(ep_schedule* s, int32_t* code, void* stream) {
   g_error.clear();
   if (!s || !code) return fail(EP_EINVAL, "null argument");
   *code = 0;
   if (!s->ws_ctl.p) return EP_OK;
-  int v[2] = {0, 0};
+  int v = 0;
   cudaStream_t st = as_stream(stream);
-  CU(cudaMemcpyAsync(v, s->ws_ctl.p, sizeof v, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&v, s->ws_ctl.as<int>() + 2, sizeof v, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
-  *code = v[1];
-  if (v[1]) {
-    CU(cudaMemsetAsync(s->ws_ctl.as<int>() + 1, 0, sizeof(int), st));
+  *code = v;
+  if (v) {
+    CU(cudaMemsetAsync(s->ws_ctl.as<int>() + 2, 0, sizeof(int), st));
     s->bacc_dirty = true;  // an interrupted launch may have left partial sums
-    return fail(EP_ETIMEOUT, "a pipelined kernel gave up waiting (code %d)", v[1]);
+    return fail(EP_ETIMEOUT, "a pipelined kernel gave up waiting (code %d)", v);
   }
   return EP_OK;
 }

@@ -67,14 +67,18 @@ __device__ __forceinline__ void vst(float* p, const float* v) {
   else
     *p = v[0];
 }
+// fire-and-forget vector reductions into global memory (no value returned,
+// so the issuing warp never waits for them)
 template <int W>
 __device__ __forceinline__ void vred(float* p, const float* v) {
   if constexpr (W == 4)
-    atomicAdd(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3])
+                 : "memory");
   else if constexpr (W == 2)
-    atomicAdd(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v[0]), "f"(v[1]) : "memory");
   else
-    atomicAdd(p, v[0]);
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v[0]) : "memory");
 }
 
 // Record r of a planar buffer of n records <-> registers v[0..D), one vector
@@ -144,7 +148,10 @@ __device__ __forceinline__ void fwd_entry(const float* xs, int64_t n, int64_t ba
 
 // Forward pull of one lane over the K columns of its slice.  xs: the state
 // planes (n records, positions offset by `base`), ix / wv: the lane's first
-// slot (the next column is 32 slots further).  Unused slots are skipped.
+// slot (the next column is 32 slots further).  Unused slots add exactly zero.
+// kSlotUnroll slots per iteration: their loads are independent, so they are
+// all in flight before the arithmetic.
+constexpr int kSlotUnroll = 2;
 template <int D, bool NC>
 __device__ __forceinline__ void fwd_slice(const float* xs, int64_t n, int64_t base,
                                           const uint16_t* ix, const float* wv, int K,
@@ -152,23 +159,21 @@ __device__ __forceinline__ void fwd_slice(const float* xs, int64_t n, int64_t ba
 #pragma unroll
   for (int c = 0; c < D; ++c) acc[c] = 0.f;
   int k = 0;
-  for (; k + 1 < K; k += 2) {  // two slots per iteration: their loads are independent
-    uint16_t e0, e1;
-    float w0, w1;
-    if constexpr (NC) {
-      e0 = __ldg(ix + 32 * k), e1 = __ldg(ix + 32 * (k + 1));
-      w0 = __ldg(wv + 32 * k), w1 = __ldg(wv + 32 * (k + 1));
-    } else {
-      e0 = ix[32 * k], e1 = ix[32 * (k + 1)];
-      w0 = wv[32 * k], w1 = wv[32 * (k + 1)];
+  for (; k + kSlotUnroll <= K; k += kSlotUnroll) {
+    uint16_t e[kSlotUnroll];
+    float wt[kSlotUnroll];
+#pragma unroll
+    for (int u = 0; u < kSlotUnroll; ++u) {
+      e[u] = NC ? __ldg(ix + 32 * (k + u)) : ix[32 * (k + u)];
+      wt[u] = NC ? __ldg(wv + 32 * (k + u)) : wv[32 * (k + u)];
     }
-    if (e0 != kSlotNone) fwd_entry<D, NC>(xs, n, base, e0, w0, xp, acc);
-    if (e1 != kSlotNone) fwd_entry<D, NC>(xs, n, base, e1, w1, xp, acc);
+#pragma unroll
+    for (int u = 0; u < kSlotUnroll; ++u) fwd_entry<D, NC>(xs, n, base, e[u], wt[u], xp, acc);
   }
-  if (k < K) {
+  for (; k < K; ++k) {
     const uint16_t e = NC ? __ldg(ix + 32 * k) : ix[32 * k];
     const float wt = NC ? __ldg(wv + 32 * k) : wv[32 * k];
-    if (e != kSlotNone) fwd_entry<D, NC>(xs, n, base, e, wt, xp, acc);
+    fwd_entry<D, NC>(xs, n, base, e, wt, xp, acc);
   }
 }
 
@@ -184,9 +189,8 @@ __device__ __forceinline__ void adj_slice(const float* xs, const float* ls, int6
                                           float* __restrict__ gslot, float tau) {
 #pragma unroll
   for (int c = 0; c < D; ++c) acc[c] = 0.f;
-  for (int k = 0; k < K; ++k) {
+  for (int k = 0; k < K; ++k) {  // an unused slot (w = 0, own position) adds zero
     const uint16_t e = ix[32 * k];
-    if (e == kSlotNone) continue;
     const float we = wv[32 * k];
     const int o = e & kSlotPos;
     float xo[D], lo[D];
@@ -216,10 +220,10 @@ __device__ __forceinline__ void adj_slice(const float* xs, const float* ls, int6
 // this block uses (and out = flux if requested), one vector reduction into the
 // accumulator of a shared vertex.
 template <int D>
-__device__ __forceinline__ void fwd_block_slice(const FluxArgs& a, const FluxDesc& d, const float* xs,
-                                                int npos, const uint16_t* ix, const float* wv,
-                                                const uint16_t* soff, const int32_t* ssid, int sl,
-                                                int lane) {
+__device__ __forceinline__ void fwd_block_slice(const FluxArgs& a, float* bacc, const FluxDesc& d,
+                                                const float* xs, int npos, const uint16_t* ix,
+                                                const float* wv, const uint16_t* soff,
+                                                const int32_t* ssid, int sl, int lane) {
   const int p = 32 * sl + lane;
   const int c0 = soff[sl], K = soff[sl + 1] - c0;
   float xp[D], acc[D];
@@ -235,7 +239,7 @@ __device__ __forceinline__ void fwd_block_slice(const FluxArgs& a, const FluxDes
     rec_store<D>(a.x_out, a.n_rec, (int64_t)d.rec_lo + p, xn);
     if (a.out) rec_store<D>(a.out, a.n_rec, (int64_t)d.rec_lo + p, acc);
   } else {
-    acc_red<D>(a.bacc, ssid[p - d.ni], acc);
+    acc_red<D>(bacc, ssid[p - d.ni] & kSidMask, acc);
   }
 }
 
@@ -244,11 +248,11 @@ __device__ __forceinline__ void fwd_block_slice(const FluxArgs& a, const FluxDes
 // block uses, one reduction into the accumulator of a shared vertex; gw is the
 // weight gradient in slot layout.
 template <int D>
-__device__ __forceinline__ void adj_block_slice(const FluxArgs& a, const FluxDesc& d, const float* xs,
-                                                const float* ls, int npos, const uint16_t* ix,
-                                                const float* wv, const uint16_t* soff,
-                                                const int32_t* ssid, float* lam, float* gw, int sl,
-                                                int lane) {
+__device__ __forceinline__ void adj_block_slice(const FluxArgs& a, float* bacc, const FluxDesc& d,
+                                                const float* xs, const float* ls, int npos,
+                                                const uint16_t* ix, const float* wv,
+                                                const uint16_t* soff, const int32_t* ssid, float* lam,
+                                                float* gw, int sl, int lane) {
   const int p = 32 * sl + lane;
   const int c0 = soff[sl], K = soff[sl + 1] - c0;
   float xp[D], lp[D], acc[D];
@@ -266,8 +270,57 @@ __device__ __forceinline__ void adj_block_slice(const FluxArgs& a, const FluxDes
     for (int c = 0; c < D; ++c) lp[c] = fmaf(a.tau, acc[c], lp[c]);
     rec_store<D>(lam, a.n_rec, (int64_t)d.rec_lo + p, lp);
   } else {
-    acc_red<D>(a.bacc, ssid[p - d.ni], acc);
+    acc_red<D>(bacc, ssid[p - d.ni] & kSidMask, acc);
   }
+}
+
+// The fold of the shared vertices over copies i0, i0 + stride, ... below i1,
+// U copies per iteration (their loads are in flight together).
+// Copy r of shared vertex h: x_out[r] = x_in[r] + tau * acc_cur[h] (every copy
+// holds the same value, so every copy ends with the same new value),
+// out[r] = acc_cur[h] if out is not null; the first copy of h clears h in
+// acc_next, the buffer the next step accumulates into.
+constexpr int kFoldUnroll = 4;  // the stand-alone fold kernel
+template <int D, int U = kFoldUnroll>
+__device__ __forceinline__ void fold_copies(const FluxArgs& a, const float* x_in, float* x_out,
+                                            float* out, const float* acc_cur, float* acc_next,
+                                            int64_t i0, int64_t i1, int64_t stride) {
+  for (int64_t i = i0; i < i1; i += U * stride) {
+    int32_t raw[U];
+    int64_t r[U];
+    float acc[U][D], x[U][D];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t j = i + u * stride;
+      raw[u] = j < i1 ? __ldg(a.fold_sid + j) : 0;
+      r[u] = j < i1 ? __ldg(a.fold_rec + j) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (r[u] >= 0) {
+        acc_load<D>(acc_cur, raw[u] & kSidMask, acc[u]);
+        rec_load<D>(x_in, a.n_rec, r[u], x[u]);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (r[u] >= 0) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) x[u][c] = fmaf(a.tau, acc[u][c], x[u][c]);
+        rec_store<D>(x_out, a.n_rec, r[u], x[u]);
+        if (out) rec_store<D>(out, a.n_rec, r[u], acc[u]);
+        if (raw[u] < 0) acc_zero<D>(acc_next, raw[u] & kSidMask);
+      }
+  }
+}
+
+// The accumulators of the shared vertices are double-buffered: the edge
+// work of a step adds into buffer (phase & 1), and the fold after it reads
+// that buffer, clears the other one for the next step and flips the phase
+// (kept in device memory, so a captured CUDA graph replays correctly whatever
+// its number of steps).
+template <int D>
+__device__ __forceinline__ float* acc_buffer(const FluxArgs& a, int phase) {
+  return a.bacc + (phase & 1) * a.n_sh * acc_stride(D);
 }
 
 }  // namespace dev

@@ -15,8 +15,9 @@
 //   consumer warps each take whole slices (32 positions) of a stage, sum the
 //                  flux of every position from shared memory (pull form),
 //                  write back (interior vertices in place, shared vertices with
-//                  one vector reduction into their accumulator), and arrive on
-//                  the stage's "empty" mbarrier.  Warps move through the
+//                  one vector reduction into their accumulator, which the
+//                  fold kernel launched next applies to every copy), and
+//                  arrive on the stage's "empty" mbarrier.  Warps move through the
 //                  stages independently (no block-wide barrier per kernel
 //                  block); slices are dealt so that every warp gets the same
 //                  share over the run.
@@ -50,14 +51,16 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps (up to the hint,
+// in ns) until the phase completes instead of spinning on the issue slots
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(saddr(bar)), "r"(parity)
+      : "r"(saddr(bar)), "r"(parity), "r"(1000000u)
       : "memory");
   return ok != 0;
 }
@@ -140,10 +143,13 @@ __device__ __forceinline__ void produce(const FluxDesc& d, const FluxArgs& a, co
 }
 
 // Shared scaffolding of the persistent kernels.  Kernel blocks are dealt
-// round-robin (block j of this CUDA block is blockIdx.x + j * gridDim.x).
-// consume(S, d, slice, lane) computes and writes back one slice.
+// round-robin (block j of this CUDA block is blockIdx.x + j * gridDim.x) to a
+// producer thread and consumer warps; consume(S, d, slice, lane, bacc)
+// computes and writes back one slice, adding the partial sums of shared
+// vertices into the accumulator buffer of this step (the fold kernel that
+// follows reads them).
 template <int D, bool ADJ, typename Consume>
-__device__ __forceinline__ void pipeline(const FluxArgs& a, const float* lam, int* err,
+__device__ __forceinline__ void pipeline(const FluxArgs& a, const float* lam_in, int* err,
                                          const TmaLayout L, Consume consume) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
@@ -163,7 +169,7 @@ __device__ __forceinline__ void pipeline(const FluxArgs& a, const float* lam, in
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (warp == 0) {
     if (lane != 0) return;
-    int fills[kMaxStages] = {0, 0, 0, 0};
+    int issued = 0;  // stage fills issued: fill i went to stage i % stages
     int64_t b = blockIdx.x;
     FluxDesc dn;
     if (b < a.k) dn = a.desc[b];
@@ -177,27 +183,31 @@ __device__ __forceinline__ void pipeline(const FluxArgs& a, const float* lam, in
       if (b >= a.k) {  // end marker
         S.desc->nv = -1;
         mbar_arrive(&full[s]);
-        ++fills[s];
+        ++issued;
         break;
       }
       if (j == L.stall) break;  // test hook: this stage is never filled
       const FluxDesc d = dn;
       if (b + G < a.k) dn = a.desc[b + G];  // next descriptor in flight while copying this one
-      produce<D>(d, a, ADJ ? lam : nullptr, S, L, &full[s]);
-      ++fills[s];
+      produce<D>(d, a, ADJ ? lam_in : nullptr, S, L, &full[s]);
+      ++issued;
     }
     // never leave the CTA with copies in flight: wait (bounded) for the last
     // fill of every stage
-    for (int s = 0; s < L.stages; ++s)
-      if (fills[s]) mbar_wait(&full[s], (uint32_t)(fills[s] - 1) & 1u);
+    for (int s = 0; s < L.stages && s < issued; ++s) {
+      const int fills = (issued - s + L.stages - 1) / L.stages;
+      mbar_wait(&full[s], (uint32_t)(fills - 1) & 1u);
+    }
     return;
   }
   // consumers
+  float* bacc = acc_buffer<D>(a, *a.phase);
   const int cw = warp - 1;
   int rot = 0;  // slices dealt so far, mod ncw
-  for (int j = 0;; ++j) {
-    const int s = j % L.stages;
-    const bool ok = mbar_wait(&full[s], (uint32_t)(j / L.stages) & 1u);
+  int s = 0;
+  uint32_t par = 0;
+  for (;;) {
+    const bool ok = mbar_wait(&full[s], par);
     if (!__all_sync(0xffffffffu, ok)) {
       if (lane == 0) atomicOr(err, kErrTimeoutFull);
       return;
@@ -207,19 +217,22 @@ __device__ __forceinline__ void pipeline(const FluxArgs& a, const float* lam, in
     if (d.nv < 0) return;
     int sl = cw - rot;
     if (sl < 0) sl += ncw;
-    for (; sl < d.nsl; sl += ncw) consume(S, d, sl, lane);
-    rot = (rot + d.nsl) % ncw;
+    for (; sl < d.nsl; sl += ncw) consume(S, d, sl, lane, bacc);
+    rot += d.nsl;
+    while (rot >= ncw) rot -= ncw;
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
+    if (++s == L.stages) s = 0, par ^= 1u;
   }
 }
 
 // ------------------------------------------------------------------ forward
 
 template <int D>
-__global__ void __launch_bounds__(1024) flux_fwd_tma_kernel(const FluxArgs a, int* err, TmaLayout L) {
-  auto consume = [&](const StageRefs& S, const FluxDesc& d, int sl, int lane) {
-    fwd_block_slice<D>(a, d, S.x, L.npos, S.sidx, S.w, S.soff, S.sid, sl, lane);
+__global__ void __maxnreg__(56) flux_fwd_tma_kernel(const FluxArgs a, int* err,
+                                                    TmaLayout L) {
+  auto consume = [&](const StageRefs& S, const FluxDesc& d, int sl, int lane, float* bacc) {
+    fwd_block_slice<D>(a, bacc, d, S.x, L.npos, S.sidx, S.w, S.soff, S.sid, sl, lane);
   };
   pipeline<D, false>(a, nullptr, err, L, consume);
 }
@@ -229,8 +242,8 @@ __global__ void __launch_bounds__(1024) flux_fwd_tma_kernel(const FluxArgs a, in
 template <int D>
 __global__ void __launch_bounds__(1024) flux_adj_tma_kernel(const FluxArgs a, float* lam, float* gw,
                                                             int* err, TmaLayout L) {
-  auto consume = [&](const StageRefs& S, const FluxDesc& d, int sl, int lane) {
-    adj_block_slice<D>(a, d, S.x, S.lam, L.npos, S.sidx, S.w, S.soff, S.sid, lam, gw, sl, lane);
+  auto consume = [&](const StageRefs& S, const FluxDesc& d, int sl, int lane, float* bacc) {
+    adj_block_slice<D>(a, bacc, d, S.x, S.lam, L.npos, S.sidx, S.w, S.soff, S.sid, lam, gw, sl, lane);
   };
   pipeline<D, true>(a, lam, err, L, consume);
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <atomic>
+#include <climits>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -15,8 +16,8 @@ namespace ep {
 //   [ni, nv)   shared vertices (p_v > 1); each kernel block holds its own copy
 //              (replica) of every shared vertex it uses, so position p is always
 //              the state record rec_lo + p and a block's vertex set is one
-//              contiguous run; sid_list[h0 + p - ni] is the shared id that
-//              indexes the accumulators and the copy lists of the fold.
+//              contiguous run; sid_list[h0 + p - ni] is the shared id h that
+//              indexes the accumulators (kSidFirst marks the first copy of h).
 // Within each class positions are ordered by descending in-block degree.
 // Incidence in sliced-ELL form: slice j holds the positions [32 j, 32 j + 32);
 // its incidence entries occupy K_j = soff[q0 + j + 1] - soff[q0 + j] columns
@@ -24,7 +25,9 @@ namespace ep {
 // warp reads one column with one access per array.  A slot holds the other
 // endpoint's position (bits 0-14) and a source flag (bit 15: this position is
 // the task's first endpoint), and the task weight in the same slot of the
-// weight layout; unused slots hold kSlotNone.  Every task has one slot at each
+// weight layout; an unused slot has weight 0 and points at its own lane's
+// position (position 0 past the block's last position), so its term is exactly
+// zero.  Every task has one slot at each
 // endpoint (one for a self loop), so the forward flux is computed from either
 // side without signs (pull form).  Every per-block segment starts on a 16-byte
 // boundary and is padded to a multiple of 16 bytes (one bulk copy each).
@@ -40,7 +43,8 @@ static_assert(sizeof(FluxDesc) == 64, "FluxDesc layout");
 // Slot fields (flux)
 constexpr uint16_t kSlotPos = 0x7fffu;
 constexpr uint16_t kSlotSrc = 0x8000u;
-constexpr uint16_t kSlotNone = 0xffffu;
+constexpr int32_t kSidFirst = INT32_MIN;   // sid_list: first copy of this shared vertex
+constexpr int32_t kSidMask = 0x7fffffff;
 
 // Incidence entry fields (SpMV rows)
 constexpr uint32_t kPosMask = 0x7fffu;
@@ -82,6 +86,7 @@ struct HostSchedule {
   std::vector<int32_t> vrec;      // record -> data vertex (-1: padding)
   std::vector<int32_t> cptr, crec;  // copies of shared vertex s: crec[cptr[s] .. cptr[s+1])
   std::vector<int32_t> sid_list;  // shared id of every shared position, per block
+  std::vector<int32_t> fold_rec, fold_sid;  // every copy: its record and shared id (fold order)
   std::vector<uint16_t> sidx;     // slot entries
   std::vector<uint16_t> soff;     // slice column offsets, per block
   std::vector<int32_t> gslot;     // task -> its source-side slot

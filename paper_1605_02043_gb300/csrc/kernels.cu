@@ -85,10 +85,11 @@ __global__ void __launch_bounds__(1024) flux_fwd_kernel(const FluxArgs a, TmaLay
   const FluxDesc d = a.desc[blockIdx.x];
   const BlockSmem S = block_smem(smem, L);
   stage_block<D>(d, a, nullptr, S, L);
+  float* bacc = acc_buffer<D>(a, *a.phase);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int sl = warp; sl < d.nsl; sl += nw)
-    fwd_block_slice<D>(a, d, S.x, L.npos, S.sidx, S.w, S.soff, S.sid, sl, lane);
+    fwd_block_slice<D>(a, bacc, d, S.x, L.npos, S.sidx, S.w, S.soff, S.sid, sl, lane);
 }
 
 // Read-only-cache variant: the texture-cache kernel of Section 5 (Fig. 7(c)),
@@ -125,36 +126,31 @@ __global__ void __launch_bounds__(1024) flux_fwd_ldg_kernel(const FluxArgs a) {
       rec_store<D>(a.x_out, a.n_rec, (int64_t)d.rec_lo + p, xn);
       if (a.out) rec_store<D>(a.out, a.n_rec, (int64_t)d.rec_lo + p, acc[i]);
     } else {
-      acc_red<D>(a.bacc, __ldg(a.sid + d.h0 + p - d.ni), acc[i]);
+      acc_red<D>(acc_buffer<D>(a, *a.phase), __ldg(a.sid + d.h0 + p - d.ni) & kSidMask, acc[i]);
     }
   }
 }
 
-// The fold of the shared vertices, one thread per shared vertex h: every copy
-// r of h gets x_out[r] = x_in[first copy] + tau * acc[h] (all copies hold the
-// same value), out[r] = acc[h] if out is not null, and acc[h] = 0.
+// The fold of the shared vertices after a one-block edge kernel, one thread
+// per copy (fold_rec / fold_sid in record order: coalesced record accesses,
+// one dependent round trip; flux_common.cuh fold_copies).  The last CUDA
+// block to finish flips the phase.
 template <int D>
-__global__ void bnd_update_kernel(const float* x_in, float* x_out, float* __restrict__ bacc,
-                                  float* __restrict__ out, const int32_t* __restrict__ cptr,
-                                  const int32_t* __restrict__ crec, int64_t n_rec, int64_t n_sh,
-                                  float tau) {
+__global__ void bnd_update_kernel(const FluxArgs a, const float* x_in, float* x_out, float* out) {
   // launched with programmatic serialisation after the edge kernel: wait for
   // it (the accumulators and records it wrote) before reading
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < n_sh;
-       h += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t c0 = cptr[h], c1 = cptr[h + 1];
-    float acc[D], x[D];
-    acc_load<D>(bacc, h, acc);
-    rec_load<D>(x_in, n_rec, crec[c0], x);
-#pragma unroll
-    for (int c = 0; c < D; ++c) x[c] = fmaf(tau, acc[c], x[c]);
-    for (int32_t i = c0; i < c1; ++i) {
-      const int32_t r = crec[i];
-      rec_store<D>(x_out, n_rec, r, x);
-      if (out) rec_store<D>(out, n_rec, r, acc);
+  const int ph = *a.phase;
+  fold_copies<D>(a, x_in, x_out, out, acc_buffer<D>(a, ph), acc_buffer<D>(a, ph ^ 1),
+                 blockIdx.x * (int64_t)blockDim.x + threadIdx.x, a.n_copies,
+                 (int64_t)gridDim.x * blockDim.x);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.phase + 1, 1) == (int)gridDim.x - 1) {
+      a.phase[0] = ph ^ 1;
+      a.phase[1] = 0;
     }
-    acc_zero<D>(bacc, h);
   }
 }
 
@@ -168,10 +164,11 @@ __global__ void __launch_bounds__(1024) flux_adj_kernel(const FluxArgs a, float*
   const FluxDesc d = a.desc[blockIdx.x];
   const BlockSmem S = block_smem(smem, L);
   stage_block<D>(d, a, lam, S, L);
+  float* bacc = acc_buffer<D>(a, *a.phase);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int sl = warp; sl < d.nsl; sl += nw)
-    adj_block_slice<D>(a, d, S.x, S.lam, L.npos, S.sidx, S.w, S.soff, S.sid, lam, gw, sl, lane);
+    adj_block_slice<D>(a, bacc, d, S.x, S.lam, L.npos, S.sidx, S.w, S.soff, S.sid, lam, gw, sl, lane);
 }
 
 // --------------------------------------------------------------------- SpMV
@@ -419,7 +416,7 @@ template <int D>
 cudaError_t fold_launch(const FluxArgs& a, float* x_out, const float* x_in, float* out, cudaStream_t st) {
   if (a.n_sh <= 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid_for(a.n_sh, 256));
+  cfg.gridDim = dim3(grid_for((a.n_copies + kFoldUnroll - 1) / kFoldUnroll, 256));
   cfg.blockDim = dim3(256);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -427,8 +424,7 @@ cudaError_t fold_launch(const FluxArgs& a, float* x_out, const float* x_in, floa
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, bnd_update_kernel<D>, x_in, x_out, a.bacc, out, a.cptr, a.crec,
-                            a.n_rec, a.n_sh, a.tau);
+  return cudaLaunchKernelEx(&cfg, bnd_update_kernel<D>, a, x_in, x_out, out);
 }
 
 template <int D>

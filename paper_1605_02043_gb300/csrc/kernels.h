@@ -27,10 +27,12 @@ struct FluxArgs {
   const float* w;        // task weights in slot layout
   const float* x_in;     // state in schedule layout (planar, n_rec records)
   float* x_out;          // may equal x_in
-  float* bacc;           // n_sh accumulator records (acc_stride(D) floats each), zero on entry and exit
+  float* bacc;           // 2 x n_sh accumulator records (acc_stride(D) floats each)
+  int* phase;            // ctl[0]: accumulator phase, ctl[1]: fold blocks finished
   float* out;            // flux in schedule layout or nullptr
-  const int32_t* cptr;   // copies of shared vertex h: crec[cptr[h] .. cptr[h+1])
-  const int32_t* crec;
+  const int32_t* fold_rec;  // every copy of a shared vertex: its record and shared id
+  const int32_t* fold_sid;
+  int64_t n_copies;
   int64_t n_rec, n_sh;
   float tau;
   int32_t max_nv, max_nslot, max_nsh, max_nsl;
@@ -69,7 +71,7 @@ struct CostArgs {
 
 // Persistent pipelined kernels (flux_tma.cu): per-stage shared-memory layout
 // (byte offsets, all multiples of 16) and launch plan.
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 8;
 struct TmaLayout {
   int npos;  // positions per state plane (multiple of 4)
   int off_lam, off_sidx, off_w, off_sid, off_soff, off_desc;
@@ -79,7 +81,7 @@ struct TmaLayout {
 };
 struct TmaPlan {
   TmaLayout L;
-  int grid, threads;
+  int grid, threads, per_sm;
   size_t smem;
   int* err;  // error word (bit 0: a "full" wait expired, bit 1: an "empty" wait expired)
   bool fits = true;  // false: two stages exceed shared memory; use the one-block kernel
@@ -94,9 +96,9 @@ const void* flux_tma_kernel_ptr(int D, bool adjoint);
 cudaError_t flux_step(const FluxArgs& a, int D, cudaStream_t st);
 // read-only-cache variant (no staging); needs max_np <= 4096
 cudaError_t flux_step_ldg(const FluxArgs& a, int D, cudaStream_t st);
-// shared-vertex fold after an edge kernel: every copy of shared vertex h
-// becomes x_in[copy] + tau * bacc[h] in x_out; out (if not null) gets bacc[h];
-// bacc[h] is zeroed
+// shared-vertex fold after an edge kernel: every copy r of shared vertex h
+// becomes x_out[r] = x_in[r] + tau * acc[h]; out[r] (if not null) = acc[h];
+// the other accumulator buffer is cleared and the phase flips
 cudaError_t bnd_update(const FluxArgs& a, int D, float* x_out, const float* x_in, float* out,
                        cudaStream_t st);
 cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st);

@@ -163,10 +163,12 @@ std::string flux_layout_blocks(HostSchedule& s) {
       if (q >= d.ni) copies[sid[v]].push_back(r);
     }
     next += d.nv;
-    // shared ids of positions [ni, nv)
+    // shared ids of positions [ni, nv); the first copy of each shared vertex
+    // (in its first block) carries kSidFirst
     pad_to(s.sid_list, 4, (int32_t)0);
     d.h0 = (int32_t)s.sid_list.size();
-    for (int32_t q = d.ni; q < d.nv; ++q) s.sid_list.push_back(sid[ord[q]]);
+    for (int32_t q = d.ni; q < d.nv; ++q)
+      s.sid_list.push_back(sid[ord[q]] | (owner[ord[q]] == b ? kSidFirst : 0));
     pad_to(s.sid_list, 4, (int32_t)0);
     // slices of 32 positions; columns = largest degree in the slice
     d.nsl = (d.nv + 31) / 32;
@@ -184,8 +186,15 @@ std::string flux_layout_blocks(HostSchedule& s) {
     pad_to(s.soff, 8, (uint16_t)0);
     d.s0 = (int32_t)s.sidx.size();  // a multiple of 32
     d.nslot = 32 * cols;
-    s.sidx.resize(s.sidx.size() + d.nslot, kSlotNone);
+    // unused slots (weight 0) point at the lane's own position, or at position
+    // 0 for lanes past the last position: their term is exactly zero, so the
+    // kernels need no test per slot
+    s.sidx.resize(s.sidx.size() + d.nslot, 0);
     s.wmap.resize(s.sidx.size(), -1);
+    for (int32_t j = 0; j < d.nsl; ++j)
+      for (int32_t c = s.soff[d.q0 + j]; c < s.soff[d.q0 + j + 1]; ++c)
+        for (int32_t l = 0; l < 32 && 32 * j + l < d.nv; ++l)
+          s.sidx[d.s0 + 32 * (int64_t)c + l] = (uint16_t)(32 * j + l);
     // fill: every task at both endpoints in task order (a self loop once);
     // col[q] counts the entries placed at position q so far
     col.assign(d.nv, 0);
@@ -224,6 +233,16 @@ std::string flux_layout_blocks(HostSchedule& s) {
   s.n_rec = align4(next);  // keeps every plane of a state buffer 16-byte aligned
   s.vrec.assign(s.n_rec, -1);
   for (int64_t v = 0; v < s.nd; ++v) s.vrec[s.rec_of[v]] = (int32_t)v;
+  // the fold's work list: every copy in record order (block runs in order)
+  s.fold_rec.clear();
+  s.fold_sid.clear();
+  for (int64_t b = 0; b < s.k; ++b) {
+    const FluxDesc& d = s.fdesc[b];
+    for (int32_t q = d.ni; q < d.nv; ++q) {
+      s.fold_rec.push_back(d.rec_lo + q);
+      s.fold_sid.push_back(s.sid_list[d.h0 + q - d.ni]);
+    }
+  }
   s.cptr.assign(n_sh + 1, 0);
   s.crec.clear();
   s.crec.reserve(s.vert_ptr.back());
