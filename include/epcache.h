@@ -276,11 +276,30 @@ int ep_weights_out_add(ep_schedule *s, const float *w_lay, float *w, void *strea
  * (x_out may equal x_in), out_lay = flux(x_in) if not NULL.  Two kernel
  * launches: the edge kernel updates the vertices only one kernel block uses
  * in place and adds the partial flux of the shared ones into schedule-owned
- * accumulators (zero between calls); the fold then writes x + tau * flux to
- * every copy of each shared vertex and clears its accumulator.
+ * accumulators; the finish then writes x + tau * flux to every copy of each
+ * shared vertex.
  */
 int ep_step(ep_schedule *s, int32_t D, const float *x_in, float *x_out, const float *w_lay,
             float *out_lay, float tau, void *stream);
+
+/*
+ * No counterpart in the paper (a launch-saving form of ep_step for loops of
+ * many steps).  Between two steps only the vertices used by one kernel block
+ * need their new value in memory; the copies of a shared vertex can wait:
+ * ep_step_pending makes one explicit step like ep_step but leaves the shared
+ * copies of x_out one step behind (pending) and launches only the edge kernel;
+ * the next step (ep_step or ep_step_pending, which accept a pending input)
+ * brings them up to date as it stages them, and ep_finish brings them up to
+ * date in memory.  x_out is a valid state only after ep_finish (or after an
+ * ep_step).  The pending sums live in the schedule's accumulators: finish a
+ * pending state before starting another one on the same schedule
+ * (ep_layout_in and ep_run discard sums still pending).  tau of ep_finish must
+ * be the last step's.  Launches inside a stream capture replay correctly for
+ * any number of steps.
+ */
+int ep_step_pending(ep_schedule *s, int32_t D, const float *x_in, float *x_out, const float *w_lay,
+                    float tau, void *stream);
+int ep_finish(ep_schedule *s, int32_t D, float *x_lay, float tau, void *stream);
 
 /*
  * SpMV in schedule layout (bipartite schedules, Section 5.2): y_lay = A x_lay
@@ -299,6 +318,15 @@ int ep_spmv(ep_schedule *s, const float *x_lay, const float *w_lay, float *y_lay
  */
 int ep_adjoint_step(ep_schedule *s, int32_t D, const float *x_lay, const float *w_lay, float *lam,
                     float *grad_w_lay, float tau, void *stream);
+
+/*
+ * No counterpart in the paper: ep_adjoint_step with the shared copies of lam
+ * left pending, and their finish (the same scheme as ep_step_pending and
+ * ep_finish, with accumulators of their own; x_lay must be a finished state).
+ */
+int ep_adjoint_step_pending(ep_schedule *s, int32_t D, const float *x_lay, const float *w_lay,
+                            float *lam, float *grad_w_lay, float tau, void *stream);
+int ep_adjoint_finish(ep_schedule *s, int32_t D, float *lam, float tau, void *stream);
 
 /*
  * No counterpart in the paper (a build-side pattern of this library): the

@@ -270,9 +270,22 @@ class Schedule:
     def weights_out_add(self, w_lay, w, stream=None):
         check(lib().ep_weights_out_add(self._h, _vp(w_lay), _vp(w), _stream(stream)))
 
-    def step(self, D: int, x_in, x_out, w_lay, out_lay=None, tau: float = 1e-3, stream=None):
-        check(lib().ep_step(self._h, D, _vp(x_in), _vp(x_out), _vp(w_lay), _vp(out_lay), tau,
-                            _stream(stream)))
+    def step(self, D: int, x_in, x_out, w_lay, out_lay=None, tau: float = 1e-3, stream=None,
+             pending: bool = False):
+        """One explicit step in schedule layout (ep_step); pending=True leaves the shared
+        copies one step behind (ep_step_pending; no out_lay): finish() before reading."""
+        if pending:
+            if out_lay is not None:
+                raise ValueError("a pending step has no flux output")
+            check(lib().ep_step_pending(self._h, D, _vp(x_in), _vp(x_out), _vp(w_lay), tau,
+                                        _stream(stream)))
+        else:
+            check(lib().ep_step(self._h, D, _vp(x_in), _vp(x_out), _vp(w_lay), _vp(out_lay), tau,
+                                _stream(stream)))
+
+    def finish(self, D: int, x_lay, tau: float = 1e-3, stream=None):
+        """Brings the shared copies of a pending state up to date (ep_finish)."""
+        check(lib().ep_finish(self._h, D, _vp(x_lay), tau, _stream(stream)))
 
     def spmv_x_in(self, x, x_lay, stream=None):
         check(lib().ep_spmv_x_in(self._h, _vp(x), _vp(x_lay), _stream(stream)))
@@ -284,9 +297,15 @@ class Schedule:
         """y_lay = A x_lay in schedule layout (bipartite schedules)."""
         check(lib().ep_spmv(self._h, _vp(x_lay), _vp(w_lay), _vp(y_lay), _stream(stream)))
 
-    def adjoint_step(self, D: int, x_lay, w_lay, lam, grad_w_lay, tau: float = 1e-3, stream=None):
-        check(lib().ep_adjoint_step(self._h, D, _vp(x_lay), _vp(w_lay), _vp(lam), _vp(grad_w_lay),
-                                    tau, _stream(stream)))
+    def adjoint_step(self, D: int, x_lay, w_lay, lam, grad_w_lay, tau: float = 1e-3, stream=None,
+                     pending: bool = False):
+        """One adjoint step (ep_adjoint_step); pending=True leaves the shared copies of lam
+        one step behind (ep_adjoint_step_pending): adjoint_finish() before reading lam."""
+        f = lib().ep_adjoint_step_pending if pending else lib().ep_adjoint_step
+        check(f(self._h, D, _vp(x_lay), _vp(w_lay), _vp(lam), _vp(grad_w_lay), tau, _stream(stream)))
+
+    def adjoint_finish(self, D: int, lam, tau: float = 1e-3, stream=None):
+        check(lib().ep_adjoint_finish(self._h, D, _vp(lam), tau, _stream(stream)))
 
 
 class PartitionJob:

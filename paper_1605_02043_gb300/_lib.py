@@ -43,7 +43,11 @@ SIGNATURES = {
     "ep_weights_in": (ctypes.c_int, [P, P, P, P]),
     "ep_weights_out_add": (ctypes.c_int, [P, P, P, P]),
     "ep_step": (ctypes.c_int, [P, I32, P, P, P, P, F32, P]),
+    "ep_step_pending": (ctypes.c_int, [P, I32, P, P, P, F32, P]),
+    "ep_finish": (ctypes.c_int, [P, I32, P, F32, P]),
     "ep_adjoint_step": (ctypes.c_int, [P, I32, P, P, P, P, F32, P]),
+    "ep_adjoint_step_pending": (ctypes.c_int, [P, I32, P, P, P, P, F32, P]),
+    "ep_adjoint_finish": (ctypes.c_int, [P, I32, P, F32, P]),
     "ep_spmv_x_in": (ctypes.c_int, [P, P, P, P]),
     "ep_spmv_y_out": (ctypes.c_int, [P, P, P, P]),
     "ep_spmv": (ctypes.c_int, [P, P, P, P, P]),

@@ -5,7 +5,9 @@ Forward keeps the state in the schedule's layout, stores a checkpoint every
 checkpoints in reverse: it recomputes the states of one segment with the
 forward kernel, then runs the hand-written adjoint kernel (same schedule, same
 access pattern) step by step back to the checkpoint.  Gradients flow to x0 and
-to the task weights w.
+to the task weights w.  Steps leave the copies of shared vertices pending
+(one launch per step); a state is finished where it is stored or read whole
+(checkpoints, recomputed states, the results).
 """
 from __future__ import annotations
 
@@ -27,8 +29,11 @@ class FluxSteps(torch.autograd.Function):
         ckpts = []
         for t in range(steps):
             if t % every == 0:
+                if t:
+                    sched.finish(D, xl, tau)
                 ckpts.append(xl.clone())
-            sched.step(D, xl, xl, wl, None, tau)
+            sched.step(D, xl, xl, wl, None, tau, pending=True)
+        sched.finish(D, xl, tau)
         xT = torch.empty_like(x0)
         sched.layout_out(xl, xT)
         ctx.sched, ctx.steps, ctx.tau, ctx.every, ctx.D = sched, steps, tau, every, D
@@ -51,7 +56,8 @@ class FluxSteps(torch.autograd.Function):
             for t in range(T - 1):
                 sched.step(D, states[t], states[t + 1], wl, None, tau)
             for t in range(T - 1, -1, -1):
-                sched.adjoint_step(D, states[t], wl, lam, gwl, tau)
+                sched.adjoint_step(D, states[t], wl, lam, gwl, tau, pending=True)
+        sched.adjoint_finish(D, lam, tau)
         dx0 = torch.empty_like(g)
         sched.layout_out(lam, dx0)
         dw = torch.zeros(sched.m, device=g.device, dtype=torch.float32)
@@ -100,8 +106,11 @@ class FluxRunner:
         self.xl.copy_(self.x0l)
         for t in range(self.steps):
             if t % self.every == 0:
+                if t:
+                    s.finish(D, self.xl, tau)
                 self.ckpt[t // self.every].copy_(self.xl)
-            s.step(D, self.xl, self.xl, self.wl, None, tau)
+            s.step(D, self.xl, self.xl, self.wl, None, tau, pending=True)
+        s.finish(D, self.xl, tau)
 
     def backward(self):
         s, D, tau = self.s, self.D, self.tau
@@ -113,7 +122,8 @@ class FluxRunner:
             for t in range(T - 1):
                 s.step(D, states[t], states[t + 1], self.wl, None, tau)
             for t in range(T - 1, -1, -1):
-                s.adjoint_step(D, states[t], self.wl, self.lam, self.gwl, tau)
+                s.adjoint_step(D, states[t], self.wl, self.lam, self.gwl, tau, pending=True)
+        s.adjoint_finish(D, self.lam, tau)
 
     def run(self):
         self.forward()

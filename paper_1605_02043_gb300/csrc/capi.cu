@@ -148,8 +148,12 @@ struct ep_schedule {
   int stages = 3;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
   int stall = -1;  // test hook of the bounded waits (ep_debug_stall)
   int cache = EP_CACHE_SMEM;  // forward flux kernel family (ep_set_cache)
-  // [0] accumulator phase, [1] fold blocks finished, [2] error word
+  // [0] forward accumulator phase, [1] adjoint accumulator phase,
+  // [2] error word, [3] CUDA blocks finished in the current launch
   DBuf ws_ctl;
+  size_t ws_bacc_set = 0;  // floats of one accumulator buffer (6 buffers: 3 forward, 3 adjoint)
+  int32_t bacc_D = 0;      // state width the accumulators were last used with
+  bool pending[2] = {false, false};  // a state of this kind was left pending
   int sm_count = 0;
   // launch plans of the pipelined kernels, cached per (D, adjoint) so that
   // steps inside a stream capture only enqueue work
@@ -229,7 +233,11 @@ cudaStream_t as_stream(void* p) { return static_cast<cudaStream_t>(p); }
 const int32_t* wmap_of(ep_schedule* s) { return s->d_wmap.as<int32_t>(); }
 int64_t wlen_of(const ep_schedule* s) { return s->h.w_pad; }
 
-ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, float* x_out,
+// accumulator sets: forward steps and adjoint steps rotate their own three
+// buffers with their own phase word
+constexpr int kFwd = 0, kAdj = 1;
+
+ep::dev::FluxArgs flux_args(ep_schedule* s, int kind, const float* w, const float* x_in, float* x_out,
                             float* out, float tau) {
   ep::dev::FluxArgs a;
   a.desc = s->d_desc.as<ep::FluxDesc>();
@@ -240,8 +248,9 @@ ep::dev::FluxArgs flux_args(ep_schedule* s, const float* w, const float* x_in, f
   a.w = w;
   a.x_in = x_in;
   a.x_out = x_out;
-  a.bacc = s->ws_bacc.as<float>();
-  a.phase = s->ws_ctl.as<int>();
+  a.bacc = s->ws_bacc.as<float>() + (size_t)kind * 3 * s->ws_bacc_set;
+  a.phase = s->ws_ctl.as<int>() + kind;
+  a.done = s->ws_ctl.as<int>() + 3;
   a.out = out;
   a.fold_rec = s->d_frec.as<int32_t>();
   a.fold_sid = s->d_fsid.as<int32_t>();
@@ -275,7 +284,7 @@ int tma_plan(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
 int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
   const ep::HostSchedule& h = s->h;
   ep::dev::TmaLayout& L = P.L;
-  L = ep::dev::tma_layout(flux_args(s, nullptr, nullptr, nullptr, nullptr, 0.f), D, adjoint);
+  L = ep::dev::tma_layout(flux_args(s, kFwd, nullptr, nullptr, nullptr, nullptr, 0.f), D, adjoint);
   if (!s->sm_count) {
     int dev = 0;
     CU(cudaGetDevice(&dev));
@@ -291,7 +300,7 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
   P.fits = (int64_t)L.stages * L.stage_bytes <= optin;
   if (!P.fits) return EP_OK;  // the launch falls back to one CUDA block per schedule block
   P.smem = (size_t)L.stages * L.stage_bytes;
-  P.threads = 32 + std::min(s->tpb, 992);  // producer warp, consumer warps
+  P.threads = 96 + std::min(s->tpb, 928);  // producer warp, two fix-up warps, consumer warps
   const void* kern = ep::dev::flux_tma_kernel_ptr(D, adjoint);
   // the limit is a per-kernel attribute shared by every schedule: open it to
   // the device maximum (the launch still asks for P.smem)
@@ -318,9 +327,15 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
 // control words: allocated; both buffers zero and the phase reset after an
 // allocation or an interrupted launch
 int ensure_bacc(ep_schedule* s, int32_t D, cudaStream_t st) {
-  const size_t bytes = 2 * (size_t)s->h.n_sh * ep::dev::acc_stride(D) * sizeof(float);
-  if (s->ws_bacc.bytes < bytes || !s->ws_bacc.p) {
-    CU(s->ws_bacc.ensure(bytes));
+  // floats of one buffer, sized for the widest accumulator record
+  const size_t set = std::max<size_t>((size_t)s->h.n_sh * ep::dev::acc_stride(D), s->ws_bacc_set);
+  if (set != s->ws_bacc_set || !s->ws_bacc.p) {
+    CU(s->ws_bacc.ensure(6 * set * sizeof(float)));
+    s->ws_bacc_set = set;
+    s->bacc_dirty = true;
+  }
+  if (D != s->bacc_D) {  // the accumulator records change shape
+    s->bacc_D = D;
     s->bacc_dirty = true;
   }
   if (!s->ws_ctl.p) {
@@ -330,6 +345,7 @@ int ensure_bacc(ep_schedule* s, int32_t D, cudaStream_t st) {
   if (s->bacc_dirty) {  // every control word but the error word
     CU(cudaMemsetAsync(s->ws_bacc.p, 0, s->ws_bacc.bytes, st));
     CU(cudaMemsetAsync(s->ws_ctl.p, 0, 2 * sizeof(int), st));
+    CU(cudaMemsetAsync(s->ws_ctl.as<int>() + 3, 0, sizeof(int), st));
     s->bacc_dirty = false;
   }
   return EP_OK;
@@ -348,43 +364,63 @@ int block_fits(ep_schedule* s, size_t need) {
   return EP_OK;
 }
 
-int flux_step_any(ep_schedule* s, int32_t D, const float* w, const float* x_in, float* x_out,
-                  float* out, float tau, cudaStream_t st) {
-  ep::dev::FluxArgs a = flux_args(s, w, x_in, x_out, out, tau);
-  if (s->cache == EP_CACHE_L1) {
-    CU(ep::dev::flux_step_ldg(a, D, st));
-    return EP_OK;
-  }
-  ep::dev::TmaPlan P;
-  if (s->stages != 0) {
-    if (int rc = tma_plan(s, D, false, P)) return rc;
-  }
-  if (s->stages == 0 || !P.fits) {
-    if (int rc = block_fits(s, ep::dev::flux_block_smem(a, D, false))) return rc;
-    CU(ep::dev::flux_step(a, D, st));
-    return EP_OK;
-  }
-  if (a.k > 0) {
-    struct Scope {
-      ep::dev::Timer* t;
-      cudaStream_t st;
-      Scope(ep::dev::Timer* t_, cudaStream_t s_) : t(t_), st(s_) {
-        if (t) t->begin(ep::dev::T_EDGE_FWD, st);
-      }
-      ~Scope() {
-        if (t) t->end(ep::dev::T_EDGE_FWD, st);
-      }
-    } sc(a.timer, st);
-    CU(ep::dev::flux_fwd_tma(a, P, D, st));
-  }
+// Finish of a pending state (flux_common.cuh, the accumulator rotation):
+// every shared copy of x_out becomes x_in's + tau * the last step's sums.
+int finish_any(ep_schedule* s, int kind, int32_t D, const float* x_in, float* x_out, float* out,
+               float tau, cudaStream_t st) {
+  ep::dev::FluxArgs a = flux_args(s, kind, nullptr, x_in, x_out, out, tau);
   CU(ep::dev::bnd_update(a, D, x_out, x_in, out, st));
   return EP_OK;
 }
 
-// One adjoint step in schedule layout.
+// A new state is about to start: sums still pending from an unfinished one
+// must not reach it.
+void fresh_state(ep_schedule* s) {
+  if (s->pending[0] || s->pending[1]) s->bacc_dirty = true;
+  s->pending[0] = s->pending[1] = false;
+}
+
+// One forward step in schedule layout.  The shared copies of x_out are left
+// one step behind (pending) unless `finish`; the edge kernels bring pending
+// copies of x_in up to date as they stage them.
+int flux_step_any(ep_schedule* s, int32_t D, const float* w, const float* x_in, float* x_out,
+                  float* out, float tau, bool finish, cudaStream_t st) {
+  ep::dev::FluxArgs a = flux_args(s, kFwd, w, x_in, x_out, out, tau);
+  if (s->cache == EP_CACHE_L1) {
+    // the read-only-cache kernel reads x_in in place: finish it first
+    if (int rc = finish_any(s, kFwd, D, x_in, const_cast<float*>(x_in), nullptr, tau, st)) return rc;
+    CU(ep::dev::flux_step_ldg(a, D, st));
+  } else {
+    ep::dev::TmaPlan P;
+    if (s->stages != 0) {
+      if (int rc = tma_plan(s, D, false, P)) return rc;
+    }
+    if (s->stages == 0 || !P.fits) {
+      if (int rc = block_fits(s, ep::dev::flux_block_smem(a, D, false))) return rc;
+      CU(ep::dev::flux_step(a, D, st));
+    } else if (a.k > 0) {
+      struct Scope {
+        ep::dev::Timer* t;
+        cudaStream_t st;
+        Scope(ep::dev::Timer* t_, cudaStream_t s_) : t(t_), st(s_) {
+          if (t) t->begin(ep::dev::T_EDGE_FWD, st);
+        }
+        ~Scope() {
+          if (t) t->end(ep::dev::T_EDGE_FWD, st);
+        }
+      } sc(a.timer, st);
+      CU(ep::dev::flux_fwd_tma(a, P, D, st));
+    }
+  }
+  if (finish) return finish_any(s, kFwd, D, x_out, x_out, out, tau, st);
+  return EP_OK;
+}
+
+// One adjoint step in schedule layout (x finished; lam's shared copies left
+// pending unless `finish`).
 int flux_adj_any(ep_schedule* s, int32_t D, const float* w, const float* x, float* lam, float* gw,
-                 float tau, cudaStream_t st) {
-  ep::dev::FluxArgs a = flux_args(s, w, x, nullptr, nullptr, tau);
+                 float tau, bool finish, cudaStream_t st) {
+  ep::dev::FluxArgs a = flux_args(s, kAdj, w, x, nullptr, nullptr, tau);
   ep::dev::TmaPlan P;
   if (s->stages != 0) {
     if (int rc = tma_plan(s, D, true, P)) return rc;
@@ -392,9 +428,7 @@ int flux_adj_any(ep_schedule* s, int32_t D, const float* w, const float* x, floa
   if (s->stages == 0 || !P.fits) {
     if (int rc = block_fits(s, ep::dev::flux_block_smem(a, D, true))) return rc;
     CU(ep::dev::flux_adjoint_step(a, D, lam, gw, st));
-    return EP_OK;
-  }
-  if (a.k > 0) {
+  } else if (a.k > 0) {
     struct Scope {
       ep::dev::Timer* t;
       cudaStream_t st;
@@ -407,7 +441,7 @@ int flux_adj_any(ep_schedule* s, int32_t D, const float* w, const float* x, floa
     } sc(a.timer, st);
     CU(ep::dev::flux_adj_tma(a, P, D, lam, gw, st));
   }
-  CU(ep::dev::bnd_update(a, D, lam, lam, nullptr, st));
+  if (finish) return finish_any(s, kAdj, D, lam, lam, nullptr, tau, st);
   return EP_OK;
 }
 
@@ -832,6 +866,7 @@ int ep_layout_in(ep_schedule* s, int32_t D, const float* x, float* x_lay, void* 
   if (!x || !x_lay) return fail(EP_EINVAL, "null argument");
   if (misaligned(x_lay)) return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
+  fresh_state(s);
   CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), s->h.nd, s->h.n_rec, D, x, x_lay,
                         as_stream(stream), s->t()));
   return EP_OK;
@@ -868,15 +903,20 @@ int ep_weights_out_add(ep_schedule* s, const float* w_lay, float* w, void* strea
   return EP_OK;
 }
 
-int ep_step(ep_schedule* s, int32_t D, const float* x_in, float* x_out, const float* w_lay,
-            float* out_lay, float tau, void* stream) {
-  g_error.clear();
+namespace {
+
+int step_checks(ep_schedule* s, int32_t D, const void* a, const void* b, const void* c,
+                const void* d) {
   if (int rc = check_flux(s, D)) return rc;
-  if (!x_in || !x_out || !w_lay) return fail(EP_EINVAL, "null argument");
-  if (misaligned(x_in) || misaligned(x_out) || misaligned(w_lay) || misaligned(out_lay))
+  if (!a || !b || !c) return fail(EP_EINVAL, "null argument");
+  if (misaligned(a) || misaligned(b) || misaligned(c) || misaligned(d))
     return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
-  if (int rc = ensure_device(s)) return rc;
-  cudaStream_t st = as_stream(stream);
+  return ensure_device(s);
+}
+
+// a forward step in schedule layout (ep_step, ep_step_pending)
+int step_entry(ep_schedule* s, int32_t D, const float* x_in, float* x_out, const float* w_lay,
+               float* out_lay, float tau, bool finish, cudaStream_t st) {
   if (int rc = ensure_bacc(s, D, st)) return rc;
   const int64_t t = s->h.n_run, nr = s->h.n_rec;
   if (nr > t) {
@@ -891,20 +931,69 @@ int ep_step(ep_schedule* s, int32_t D, const float* x_in, float* x_out, const fl
         CU(cudaMemcpyAsync(x_out + off, x_in + off, bytes, cudaMemcpyDeviceToDevice, st));
     }
   }
-  return flux_step_any(s, D, w_lay, x_in, x_out, out_lay, tau, st);
+  if (int rc = flux_step_any(s, D, w_lay, x_in, x_out, out_lay, tau, finish, st)) return rc;
+  s->pending[kFwd] = !finish;
+  return EP_OK;
+}
+
+}  // namespace
+
+int ep_step(ep_schedule* s, int32_t D, const float* x_in, float* x_out, const float* w_lay,
+            float* out_lay, float tau, void* stream) {
+  g_error.clear();
+  if (int rc = step_checks(s, D, x_in, x_out, w_lay, out_lay)) return rc;
+  return step_entry(s, D, x_in, x_out, w_lay, out_lay, tau, true, as_stream(stream));
+}
+
+int ep_step_pending(ep_schedule* s, int32_t D, const float* x_in, float* x_out, const float* w_lay,
+                    float tau, void* stream) {
+  g_error.clear();
+  if (int rc = step_checks(s, D, x_in, x_out, w_lay, nullptr)) return rc;
+  return step_entry(s, D, x_in, x_out, w_lay, nullptr, tau, false, as_stream(stream));
+}
+
+int ep_finish(ep_schedule* s, int32_t D, float* x_lay, float tau, void* stream) {
+  g_error.clear();
+  if (int rc = step_checks(s, D, x_lay, x_lay, x_lay, nullptr)) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (int rc = ensure_bacc(s, D, st)) return rc;
+  if (int rc = finish_any(s, kFwd, D, x_lay, x_lay, nullptr, tau, st)) return rc;
+  s->pending[kFwd] = false;
+  return EP_OK;
 }
 
 int ep_adjoint_step(ep_schedule* s, int32_t D, const float* x_lay, const float* w_lay, float* lam,
                     float* grad_w_lay, float tau, void* stream) {
   g_error.clear();
-  if (int rc = check_flux(s, D)) return rc;
-  if (!x_lay || !w_lay || !lam || !grad_w_lay) return fail(EP_EINVAL, "null argument");
-  if (misaligned(x_lay) || misaligned(w_lay) || misaligned(lam) || misaligned(grad_w_lay))
-    return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
-  if (int rc = ensure_device(s)) return rc;
+  if (int rc = step_checks(s, D, x_lay, w_lay, lam, grad_w_lay)) return rc;
+  if (!grad_w_lay) return fail(EP_EINVAL, "null argument");
   cudaStream_t st = as_stream(stream);
   if (int rc = ensure_bacc(s, D, st)) return rc;
-  return flux_adj_any(s, D, w_lay, x_lay, lam, grad_w_lay, tau, st);
+  if (int rc = flux_adj_any(s, D, w_lay, x_lay, lam, grad_w_lay, tau, true, st)) return rc;
+  s->pending[kAdj] = false;
+  return EP_OK;
+}
+
+int ep_adjoint_step_pending(ep_schedule* s, int32_t D, const float* x_lay, const float* w_lay,
+                            float* lam, float* grad_w_lay, float tau, void* stream) {
+  g_error.clear();
+  if (int rc = step_checks(s, D, x_lay, w_lay, lam, grad_w_lay)) return rc;
+  if (!grad_w_lay) return fail(EP_EINVAL, "null argument");
+  cudaStream_t st = as_stream(stream);
+  if (int rc = ensure_bacc(s, D, st)) return rc;
+  if (int rc = flux_adj_any(s, D, w_lay, x_lay, lam, grad_w_lay, tau, false, st)) return rc;
+  s->pending[kAdj] = true;
+  return EP_OK;
+}
+
+int ep_adjoint_finish(ep_schedule* s, int32_t D, float* lam, float tau, void* stream) {
+  g_error.clear();
+  if (int rc = step_checks(s, D, lam, lam, lam, nullptr)) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (int rc = ensure_bacc(s, D, st)) return rc;
+  if (int rc = finish_any(s, kAdj, D, lam, lam, nullptr, tau, st)) return rc;
+  s->pending[kAdj] = false;
+  return EP_OK;
 }
 
 int ep_run(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out, int32_t D,
@@ -932,14 +1021,17 @@ int ep_run(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out,
   if (out) {
     CU(s->ws_out.ensure(lay));
   }
+  fresh_state(s);
   if (int rc = ensure_bacc(s, D, st)) return rc;
   CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, x, s->ws_x.as<float>(), st, s->t()));
   CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
   if (out) CU(cudaMemsetAsync(s->ws_out.p, 0, lay, st));
+  // the shared copies stay pending between steps; the last step finishes them
   for (int32_t t = 0; t < steps; ++t) {
-    float* o = (out && t == steps - 1) ? s->ws_out.as<float>() : nullptr;
+    const bool last = t == steps - 1;
+    float* o = (out && last) ? s->ws_out.as<float>() : nullptr;
     if (int rc = flux_step_any(s, D, s->ws_w.as<float>(), s->ws_x.as<float>(), s->ws_x.as<float>(), o,
-                               tau, st))
+                               tau, last, st))
       return rc;
   }
   CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, s->ws_x.as<float>(), x, st, s->t()));
@@ -985,20 +1077,23 @@ int ep_run_adjoint(ep_schedule* s, const float* x0, const float* w, float* lam, 
   CU(s->ws_lam.ensure(lay * sizeof(float)));
   CU(s->ws_w.ensure((size_t)wlen_of(s) * sizeof(float)));
   CU(s->ws_gw.ensure((size_t)wlen_of(s) * sizeof(float)));
+  fresh_state(s);
   if (int rc = ensure_bacc(s, D, st)) return rc;
   float* hist = s->ws_hist.as<float>();
   CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, x0, hist, st, s->t()));
   CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
   CU(cudaMemsetAsync(s->ws_gw.p, 0, (size_t)wlen_of(s) * sizeof(float), st));
+  // the recomputed states are read whole by the adjoint: finish every one
   for (int32_t t = 0; t + 1 < steps; ++t)
     if (int rc = flux_step_any(s, D, s->ws_w.as<float>(), hist + lay * t, hist + lay * (t + 1), nullptr,
-                               tau, st))
+                               tau, true, st))
       return rc;
   CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, lam, s->ws_lam.as<float>(), st,
                             s->t()));
+  // the cotangent's shared copies stay pending between adjoint steps
   for (int32_t t = steps - 1; t >= 0; --t)
     if (int rc = flux_adj_any(s, D, s->ws_w.as<float>(), hist + lay * t, s->ws_lam.as<float>(),
-                              s->ws_gw.as<float>(), tau, st))
+                              s->ws_gw.as<float>(), tau, t == 0, st))
       return rc;
   CU(ep::dev::layout_out(s->d_rec.as<int32_t>(), h.nd, h.n_rec, D, s->ws_lam.as<float>(), lam, st, s->t()));
   CU(ep::dev::gather_add(s->d_gslot.as<int32_t>(), h.m, s->ws_gw.as<float>(), grad_w, st, s->t()));

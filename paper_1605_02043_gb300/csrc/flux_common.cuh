@@ -215,10 +215,12 @@ __device__ __forceinline__ void adj_slice(const float* xs, const float* ls, int6
 
 // One slice of a forward kernel block staged in shared memory (xs: state
 // planes of npos positions, ix / wv / soff / ssid: the block's slots, slot
-// weights, slice offsets and shared ids): lane `lane` sums the flux at its
-// position and writes back, x_out = x + tau * flux in place for a vertex only
-// this block uses (and out = flux if requested), one vector reduction into the
-// accumulator of a shared vertex.
+// weights, slice offsets and shared ids; the shared copies already brought up
+// to date by fixup_copies): lane `lane` sums the flux at its position and
+// writes back, x_out = x + tau * flux in place for a vertex only this block
+// uses (and out = flux if requested); for a shared vertex one vector
+// reduction of its partial flux into this step's accumulator, and its
+// up-to-date value into this block's copy.
 template <int D>
 __device__ __forceinline__ void fwd_block_slice(const FluxArgs& a, float* bacc, const FluxDesc& d,
                                                 const float* xs, int npos, const uint16_t* ix,
@@ -240,13 +242,15 @@ __device__ __forceinline__ void fwd_block_slice(const FluxArgs& a, float* bacc, 
     if (a.out) rec_store<D>(a.out, a.n_rec, (int64_t)d.rec_lo + p, acc);
   } else {
     acc_red<D>(bacc, ssid[p - d.ni] & kSidMask, acc);
+    rec_store<D>(a.x_out, a.n_rec, (int64_t)d.rec_lo + p, xp);  // this copy, brought up to date
   }
 }
 
 // One slice of an adjoint kernel block staged in shared memory (xs, ls: state
-// and cotangent planes): lam_p += tau * acc in place for a vertex only this
-// block uses, one reduction into the accumulator of a shared vertex; gw is the
-// weight gradient in slot layout.
+// and cotangent planes, the cotangent copies already brought up to date):
+// lam_p += tau * acc in place for a vertex only this block uses; for a shared
+// vertex one reduction into this step's accumulator and its up-to-date value
+// into this block's copy; gw is the weight gradient in slot layout.
 template <int D>
 __device__ __forceinline__ void adj_block_slice(const FluxArgs& a, float* bacc, const FluxDesc& d,
                                                 const float* xs, const float* ls, int npos,
@@ -271,20 +275,77 @@ __device__ __forceinline__ void adj_block_slice(const FluxArgs& a, float* bacc, 
     rec_store<D>(lam, a.n_rec, (int64_t)d.rec_lo + p, lp);
   } else {
     acc_red<D>(bacc, ssid[p - d.ni] & kSidMask, acc);
+    rec_store<D>(lam, a.n_rec, (int64_t)d.rec_lo + p, lp);  // this copy, brought up to date
   }
 }
 
-// The fold of the shared vertices over copies i0, i0 + stride, ... below i1,
-// U copies per iteration (their loads are in flight together).
-// Copy r of shared vertex h: x_out[r] = x_in[r] + tau * acc_cur[h] (every copy
-// holds the same value, so every copy ends with the same new value),
-// out[r] = acc_cur[h] if out is not null; the first copy of h clears h in
-// acc_next, the buffer the next step accumulates into.
-constexpr int kFoldUnroll = 4;  // the stand-alone fold kernel
+// Shared vertices between steps.  Each kernel block keeps its own copy of
+// every shared vertex it uses; an edge kernel adds the block's partial sums
+// for them into an accumulator and leaves the copies one step behind
+// ("pending"): the next edge kernel brings each staged copy up to date
+// (x += tau * accumulator of the previous step) before it computes, and a
+// finish pass does the same in memory when the state itself is needed.  The
+// accumulators rotate through three buffers, with the phase Q (0..2) of each
+// kind (forward, adjoint) in device memory, so a captured CUDA graph replays
+// correctly whatever its number of steps:
+//   an edge kernel at phase Q  reads buffer Q+2 (the previous step's sums),
+//                              adds into buffer Q, and the first copy of each
+//                              shared vertex clears it in buffer Q+1;
+//   a finish at phase Q        reads buffer Q+2 into every copy and clears
+//                              buffer Q+1;
+//   both then advance the phase to Q+1 (indices mod 3).
+// The buffer an edge kernel clears was last read by the step before it, the
+// one it adds into was cleared by the step before it, and a finish leaves the
+// buffer the next step reads cleared, so no buffer is ever read and cleared
+// by the same launch.
+__device__ __forceinline__ int acc_slot(int q) { return q % 3; }
+template <int D>
+__device__ __forceinline__ float* acc_buffer(const FluxArgs& a, int q) {
+  return a.bacc + acc_slot(q) * a.n_sh * acc_stride(D);
+}
+
+// Brings the staged copies of shared positions [ni, nv) up to date in shared
+// memory (xs, npos positions per plane): x += tau * prev[h]; the first copy of
+// h clears h in `next`.  Positions ni + i0, ni + i0 + stride, ..., up to four
+// per iteration with their loads in flight together.
+template <int D>
+__device__ __forceinline__ void fixup_copies(const FluxDesc& d, float* xs, int npos, const int32_t* ssid,
+                                             const float* prev, float* next, float tau, int i0,
+                                             int stride) {
+  const int nsh = d.nv - d.ni;
+  for (int i = i0; i < nsh; i += 4 * stride) {
+    int32_t raw[4];
+    float acc[4][D];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = i + u * stride;
+      raw[u] = j < nsh ? ssid[j] : 0;
+      if (j < nsh) acc_load<D>(prev, raw[u] & kSidMask, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = i + u * stride;
+      if (j >= nsh) continue;
+      float x[D];
+      rec_load<D>(xs, npos, d.ni + j, x);
+#pragma unroll
+      for (int c = 0; c < D; ++c) x[c] = fmaf(tau, acc[u][c], x[c]);
+      rec_store<D>(xs, npos, d.ni + j, x);
+      if (raw[u] < 0) acc_zero<D>(next, raw[u] & kSidMask);
+    }
+  }
+}
+
+// The finish over copies i0, i0 + stride, ... below i1, U copies per
+// iteration (their loads are in flight together).  Copy r of shared vertex h:
+// x_out[r] = x_in[r] + tau * prev[h] (every copy holds the same value, so every
+// copy ends with the same new value), out[r] = prev[h] if out is not null;
+// the first copy of h clears h in `next`.
+constexpr int kFoldUnroll = 4;
 template <int D, int U = kFoldUnroll>
 __device__ __forceinline__ void fold_copies(const FluxArgs& a, const float* x_in, float* x_out,
-                                            float* out, const float* acc_cur, float* acc_next,
-                                            int64_t i0, int64_t i1, int64_t stride) {
+                                            float* out, const float* prev, float* next, int64_t i0,
+                                            int64_t i1, int64_t stride) {
   for (int64_t i = i0; i < i1; i += U * stride) {
     int32_t raw[U];
     int64_t r[U];
@@ -298,7 +359,7 @@ __device__ __forceinline__ void fold_copies(const FluxArgs& a, const float* x_in
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (r[u] >= 0) {
-        acc_load<D>(acc_cur, raw[u] & kSidMask, acc[u]);
+        acc_load<D>(prev, raw[u] & kSidMask, acc[u]);
         rec_load<D>(x_in, a.n_rec, r[u], x[u]);
       }
 #pragma unroll
@@ -308,19 +369,22 @@ __device__ __forceinline__ void fold_copies(const FluxArgs& a, const float* x_in
         for (int c = 0; c < D; ++c) x[u][c] = fmaf(a.tau, acc[u][c], x[u][c]);
         rec_store<D>(x_out, a.n_rec, r[u], x[u]);
         if (out) rec_store<D>(out, a.n_rec, r[u], acc[u]);
-        if (raw[u] < 0) acc_zero<D>(acc_next, raw[u] & kSidMask);
+        if (raw[u] < 0) acc_zero<D>(next, raw[u] & kSidMask);
       }
   }
 }
 
-// The accumulators of the shared vertices are double-buffered: the edge
-// work of a step adds into buffer (phase & 1), and the fold after it reads
-// that buffer, clears the other one for the next step and flips the phase
-// (kept in device memory, so a captured CUDA graph replays correctly whatever
-// its number of steps).
-template <int D>
-__device__ __forceinline__ float* acc_buffer(const FluxArgs& a, int phase) {
-  return a.bacc + (phase & 1) * a.n_sh * acc_stride(D);
+// End of a launch that uses the phase: the last CUDA block to get here
+// advances it (every block has read it by then).  Called by every thread.
+__device__ __forceinline__ void advance_phase(const FluxArgs& a, int q) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.done, 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1) {
+      *a.phase = acc_slot(q + 1);
+      *a.done = 0;
+    }
+  }
 }
 
 }  // namespace dev

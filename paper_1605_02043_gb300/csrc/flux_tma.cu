@@ -35,6 +35,7 @@ namespace dev {
 namespace {
 
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int kFixupWarps = 2;
 constexpr int kErrTimeoutFull = 1;
 constexpr int kErrTimeoutEmpty = 2;
 
@@ -143,22 +144,34 @@ __device__ __forceinline__ void produce(const FluxDesc& d, const FluxArgs& a, co
 }
 
 // Shared scaffolding of the persistent kernels.  Kernel blocks are dealt
-// round-robin (block j of this CUDA block is blockIdx.x + j * gridDim.x) to a
-// producer thread and consumer warps; consume(S, d, slice, lane, bacc)
-// computes and writes back one slice, adding the partial sums of shared
-// vertices into the accumulator buffer of this step (the fold kernel that
-// follows reads them).
+// round-robin (block j of this CUDA block is blockIdx.x + j * gridDim.x).
+//   warp 0, lane 0: producer, fills the stages with bulk copies ("full");
+//   warps 1..kFixupWarps: fix-up, bring the staged copies of shared vertices
+//           up to date from the previous step's accumulator (flux_common.cuh)
+//           while the consumers work on earlier stages, then mark the stage
+//           "ready".  Fix-up warp f owns the stages s with s % kFixupWarps ==
+//           f and takes their fills in order: a parity wait only tells the
+//           current phase from the one before it, so every fill of a stage
+//           must be awaited by one thread in order (two warps keep two
+//           stages' gathers in flight);
+//   the other warps: consumers, consume(S, d, slice, lane, acc) computes and writes
+//           back one slice, adding the partial sums of shared vertices into
+//           this step's accumulator; the last consumer warp done with a stage
+//           lets the producer refill it ("empty").
+// fix: the planes (state, or cotangent for the adjoint) whose copies are
+// pending.  Ends with the phase advance.
 template <int D, bool ADJ, typename Consume>
 __device__ __forceinline__ void pipeline(const FluxArgs& a, const float* lam_in, int* err,
                                          const TmaLayout L, Consume consume) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+  __shared__ __align__(8) uint64_t full[kMaxStages], ready[kMaxStages], empty[kMaxStages];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ncw = (int)(blockDim.x >> 5) - 1;  // consumer warps
+  const int ncw = (int)(blockDim.x >> 5) - 1 - kFixupWarps;  // consumer warps
   const int64_t G = gridDim.x;
   if (threadIdx.x == 0) {
     for (int s = 0; s < L.stages; ++s) {
       mbar_init(&full[s], 1);
+      mbar_init(&ready[s], 1);
       mbar_init(&empty[s], (uint32_t)ncw);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -167,63 +180,91 @@ __device__ __forceinline__ void pipeline(const FluxArgs& a, const float* lam_in,
   // launched with programmatic serialisation: wait for the previous kernel on
   // the stream (its writes to the state and the accumulators) first
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int q = *a.phase;
   if (warp == 0) {
-    if (lane != 0) return;
-    int issued = 0;  // stage fills issued: fill i went to stage i % stages
-    int64_t b = blockIdx.x;
-    FluxDesc dn;
-    if (b < a.k) dn = a.desc[b];
-    for (int j = 0;; ++j, b += G) {
+    if (lane == 0) {
+      int issued = 0;  // stage fills issued: fill i went to stage i % stages
+      int64_t b = blockIdx.x;
+      FluxDesc dn;
+      if (b < a.k) dn = a.desc[b];
+      for (int j = 0;; ++j, b += G) {
+        const int s = j % L.stages;
+        if (j >= L.stages && !mbar_wait(&empty[s], (uint32_t)((j / L.stages) - 1) & 1u)) {
+          atomicOr(err, kErrTimeoutEmpty);
+          break;
+        }
+        const StageRefs S = stage_refs(smem, L, s);
+        if (b >= a.k) {  // end markers, one in every stage (each fix-up warp owns stages)
+          S.desc->nv = -1;
+          mbar_arrive(&full[s]);
+          ++issued;
+          if (b >= a.k + (int64_t)(L.stages - 1) * G) break;
+          continue;
+        }
+        if (j == L.stall) break;  // test hook: this stage is never filled
+        const FluxDesc d = dn;
+        if (b + G < a.k) dn = a.desc[b + G];  // next descriptor in flight while copying this one
+        produce<D>(d, a, ADJ ? lam_in : nullptr, S, L, &full[s]);
+        ++issued;
+      }
+      // never leave the CTA with copies in flight: wait (bounded) for the last
+      // fill of every stage
+      for (int s = 0; s < L.stages && s < issued; ++s) {
+        const int fills = (issued - s + L.stages - 1) / L.stages;
+        mbar_wait(&full[s], (uint32_t)(fills - 1) & 1u);
+      }
+    }
+    __syncwarp();
+  } else if (warp <= kFixupWarps) {
+    const float* prev = acc_buffer<D>(a, q + 2);
+    float* next = acc_buffer<D>(a, q + 1);
+    for (int j = 0;; ++j) {
       const int s = j % L.stages;
-      if (j >= L.stages && !mbar_wait(&empty[s], (uint32_t)((j / L.stages) - 1) & 1u)) {
-        atomicOr(err, kErrTimeoutEmpty);
+      if (s % kFixupWarps != warp - 1) continue;
+      const uint32_t par = (uint32_t)(j / L.stages) & 1u;
+      const bool ok = mbar_wait(&full[s], par);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicOr(err, kErrTimeoutFull);
         break;
       }
       const StageRefs S = stage_refs(smem, L, s);
-      if (b >= a.k) {  // end marker
-        S.desc->nv = -1;
-        mbar_arrive(&full[s]);
-        ++issued;
+      const FluxDesc d = *S.desc;
+      if (d.nv >= 0) {
+        fixup_copies<D>(d, ADJ ? S.lam : S.x, L.npos, S.sid, prev, next, a.tau, lane, 32);
+        // the stage is written through the generic proxy here and refilled
+        // through the async proxy later
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ready[s]);
+      if (d.nv < 0) break;
+    }
+  } else {
+    float* acc = acc_buffer<D>(a, q);
+    const int cw = warp - 1 - kFixupWarps;
+    int rot = 0;  // slices dealt so far, mod ncw
+    int s = 0;
+    uint32_t par = 0;
+    for (;;) {
+      const bool ok = mbar_wait(&ready[s], par) && mbar_wait(&full[s], par);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicOr(err, kErrTimeoutFull);
         break;
       }
-      if (j == L.stall) break;  // test hook: this stage is never filled
-      const FluxDesc d = dn;
-      if (b + G < a.k) dn = a.desc[b + G];  // next descriptor in flight while copying this one
-      produce<D>(d, a, ADJ ? lam_in : nullptr, S, L, &full[s]);
-      ++issued;
+      const StageRefs S = stage_refs(smem, L, s);
+      const FluxDesc d = *S.desc;
+      if (d.nv < 0) break;
+      int sl = cw - rot;
+      if (sl < 0) sl += ncw;
+      for (; sl < d.nsl; sl += ncw) consume(S, d, sl, lane, acc);
+      rot += d.nsl;
+      while (rot >= ncw) rot -= ncw;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      if (++s == L.stages) s = 0, par ^= 1u;
     }
-    // never leave the CTA with copies in flight: wait (bounded) for the last
-    // fill of every stage
-    for (int s = 0; s < L.stages && s < issued; ++s) {
-      const int fills = (issued - s + L.stages - 1) / L.stages;
-      mbar_wait(&full[s], (uint32_t)(fills - 1) & 1u);
-    }
-    return;
   }
-  // consumers
-  float* bacc = acc_buffer<D>(a, *a.phase);
-  const int cw = warp - 1;
-  int rot = 0;  // slices dealt so far, mod ncw
-  int s = 0;
-  uint32_t par = 0;
-  for (;;) {
-    const bool ok = mbar_wait(&full[s], par);
-    if (!__all_sync(0xffffffffu, ok)) {
-      if (lane == 0) atomicOr(err, kErrTimeoutFull);
-      return;
-    }
-    const StageRefs S = stage_refs(smem, L, s);
-    const FluxDesc d = *S.desc;
-    if (d.nv < 0) return;
-    int sl = cw - rot;
-    if (sl < 0) sl += ncw;
-    for (; sl < d.nsl; sl += ncw) consume(S, d, sl, lane, bacc);
-    rot += d.nsl;
-    while (rot >= ncw) rot -= ncw;
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
-    if (++s == L.stages) s = 0, par ^= 1u;
-  }
+  advance_phase(a, q);
 }
 
 // ------------------------------------------------------------------ forward

@@ -76,31 +76,39 @@ __device__ __forceinline__ void stage_block(const FluxDesc& d, const FluxArgs& a
 
 // ------------------------------------------------------------- flux forward
 
-// One CUDA block per kernel block: stage, then every warp takes slices of 32
-// positions (pull form, flux_common.cuh).  Only the staged copy is read, so
-// the in-place update of the interior records cannot overtake a read.
+// One CUDA block per kernel block: stage, bring the pending shared copies up
+// to date, then every warp takes slices of 32 positions (pull form,
+// flux_common.cuh).  Only the staged copy is read, so the in-place update of
+// the interior records cannot overtake a read.
 template <int D>
 __global__ void __launch_bounds__(1024) flux_fwd_kernel(const FluxArgs a, TmaLayout L) {
   extern __shared__ __align__(128) unsigned char smem[];
   const FluxDesc d = a.desc[blockIdx.x];
   const BlockSmem S = block_smem(smem, L);
+  const int q = *a.phase;
   stage_block<D>(d, a, nullptr, S, L);
-  float* bacc = acc_buffer<D>(a, *a.phase);
+  __syncthreads();
+  fixup_copies<D>(d, S.x, L.npos, S.sid, acc_buffer<D>(a, q + 2), acc_buffer<D>(a, q + 1), a.tau,
+                  threadIdx.x, blockDim.x);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int sl = warp; sl < d.nsl; sl += nw)
-    fwd_block_slice<D>(a, bacc, d, S.x, L.npos, S.sidx, S.w, S.soff, S.sid, sl, lane);
+    fwd_block_slice<D>(a, acc_buffer<D>(a, q), d, S.x, L.npos, S.sidx, S.w, S.soff, S.sid, sl, lane);
+  advance_phase(a, q);
 }
 
 // Read-only-cache variant: the texture-cache kernel of Section 5 (Fig. 7(c)),
 // with the read-only data cache (ld.global.nc) in place of texture binding.
 // No staging: slots, weights and states are read from global memory through
-// that cache.  Warp w takes slices w, w + W, ..., up to R of them, and keeps
-// their sums in registers; writes wait for a block barrier, because interior
-// records are updated in place and other warps may still be reading them.
+// that cache, so it runs on a finished state (no pending copies: the previous
+// step's accumulator is zero).  Warp w takes slices w, w + W, ..., up to R of
+// them, and keeps their sums in registers; writes wait for a block barrier,
+// because interior records are updated in place and other warps may still be
+// reading them.
 template <int D, int R>
 __global__ void __launch_bounds__(1024) flux_fwd_ldg_kernel(const FluxArgs a) {
   const FluxDesc d = a.desc[blockIdx.x];
+  const int q = *a.phase;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   float xp[R][D], acc[R][D];
 #pragma unroll
@@ -125,50 +133,53 @@ __global__ void __launch_bounds__(1024) flux_fwd_ldg_kernel(const FluxArgs a) {
       for (int c = 0; c < D; ++c) xn[c] = fmaf(a.tau, acc[i][c], xp[i][c]);
       rec_store<D>(a.x_out, a.n_rec, (int64_t)d.rec_lo + p, xn);
       if (a.out) rec_store<D>(a.out, a.n_rec, (int64_t)d.rec_lo + p, acc[i]);
-    } else {
-      acc_red<D>(acc_buffer<D>(a, *a.phase), __ldg(a.sid + d.h0 + p - d.ni) & kSidMask, acc[i]);
+    } else {  // this step's sum, the clearing, and the copy (x_out may be another buffer)
+      const int32_t raw = __ldg(a.sid + d.h0 + p - d.ni);
+      acc_red<D>(acc_buffer<D>(a, q), raw & kSidMask, acc[i]);
+      if (raw < 0) acc_zero<D>(acc_buffer<D>(a, q + 1), raw & kSidMask);
+      rec_store<D>(a.x_out, a.n_rec, (int64_t)d.rec_lo + p, xp[i]);
     }
   }
+  advance_phase(a, q);
 }
 
-// The fold of the shared vertices after a one-block edge kernel, one thread
-// per copy (fold_rec / fold_sid in record order: coalesced record accesses,
-// one dependent round trip; flux_common.cuh fold_copies).  The last CUDA
-// block to finish flips the phase.
+// The finish of a pending state, one thread per copy (fold_rec / fold_sid in
+// record order: coalesced record accesses, one dependent round trip;
+// flux_common.cuh fold_copies and the accumulator rotation).
 template <int D>
 __global__ void bnd_update_kernel(const FluxArgs a, const float* x_in, float* x_out, float* out) {
   // launched with programmatic serialisation after the edge kernel: wait for
   // it (the accumulators and records it wrote) before reading
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  const int ph = *a.phase;
-  fold_copies<D>(a, x_in, x_out, out, acc_buffer<D>(a, ph), acc_buffer<D>(a, ph ^ 1),
+  const int q = *a.phase;
+  fold_copies<D>(a, x_in, x_out, out, acc_buffer<D>(a, q + 2), acc_buffer<D>(a, q + 1),
                  blockIdx.x * (int64_t)blockDim.x + threadIdx.x, a.n_copies,
                  (int64_t)gridDim.x * blockDim.x);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(a.phase + 1, 1) == (int)gridDim.x - 1) {
-      a.phase[0] = ph ^ 1;
-      a.phase[1] = 0;
-    }
-  }
+  advance_phase(a, q);
 }
 
 // ------------------------------------------------------------- flux adjoint
 
-// One CUDA block per kernel block, the adjoint step (flux_common.cuh adj_*).
+// One CUDA block per kernel block, the adjoint step (flux_common.cuh adj_*):
+// stage the state (finished) and the cotangent (copies pending), bring the
+// cotangent copies up to date, compute.
 template <int D>
 __global__ void __launch_bounds__(1024) flux_adj_kernel(const FluxArgs a, float* lam, float* gw,
                                                         TmaLayout L) {
   extern __shared__ __align__(128) unsigned char smem[];
   const FluxDesc d = a.desc[blockIdx.x];
   const BlockSmem S = block_smem(smem, L);
+  const int q = *a.phase;
   stage_block<D>(d, a, lam, S, L);
-  float* bacc = acc_buffer<D>(a, *a.phase);
+  __syncthreads();
+  fixup_copies<D>(d, S.lam, L.npos, S.sid, acc_buffer<D>(a, q + 2), acc_buffer<D>(a, q + 1), a.tau,
+                  threadIdx.x, blockDim.x);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int sl = warp; sl < d.nsl; sl += nw)
-    adj_block_slice<D>(a, bacc, d, S.x, S.lam, L.npos, S.sidx, S.w, S.soff, S.sid, lam, gw, sl, lane);
+    adj_block_slice<D>(a, acc_buffer<D>(a, q), d, S.x, S.lam, L.npos, S.sidx, S.w, S.soff, S.sid, lam,
+                       gw, sl, lane);
+  advance_phase(a, q);
 }
 
 // --------------------------------------------------------------------- SpMV
@@ -411,7 +422,7 @@ struct Scope {
   }
 };
 
-// PDL launch of the fold (the edge kernel before it may still be draining)
+// PDL launch of the finish (the edge kernel before it may still be draining)
 template <int D>
 cudaError_t fold_launch(const FluxArgs& a, float* x_out, const float* x_in, float* out, cudaStream_t st) {
   if (a.n_sh <= 0) return cudaSuccess;
@@ -438,8 +449,7 @@ cudaError_t flux_step_t(const FluxArgs& a, cudaStream_t st) {
     flux_fwd_kernel<D><<<(unsigned)a.k, a.tpb, smem, st>>>(a, L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  Scope sc(a.timer, T_BND, st);
-  return fold_launch<D>(a, a.x_out, a.x_in, a.out, st);
+  return cudaSuccess;
 }
 
 template <int D, int R>
@@ -461,11 +471,9 @@ cudaError_t flux_step_ldg_t(const FluxArgs& a, cudaStream_t st) {
       case 4: flux_ldg_launch<D, 4>(a, threads, st); break;
       default: return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
   }
-  Scope sc(a.timer, T_BND, st);
-  return fold_launch<D>(a, a.x_out, a.x_in, a.out, st);
+  return cudaSuccess;
 }
 
 template <int D>
@@ -479,8 +487,7 @@ cudaError_t flux_adj_t(const FluxArgs& a, float* lam, float* gw, cudaStream_t st
     flux_adj_kernel<D><<<(unsigned)a.k, a.tpb, smem, st>>>(a, lam, gw, L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  Scope sc(a.timer, T_BND, st);
-  return fold_launch<D>(a, lam, lam, nullptr, st);
+  return cudaSuccess;
 }
 
 }  // namespace

@@ -27,8 +27,9 @@ struct FluxArgs {
   const float* w;        // task weights in slot layout
   const float* x_in;     // state in schedule layout (planar, n_rec records)
   float* x_out;          // may equal x_in
-  float* bacc;           // 2 x n_sh accumulator records (acc_stride(D) floats each)
-  int* phase;            // ctl[0]: accumulator phase, ctl[1]: fold blocks finished
+  float* bacc;           // 3 x n_sh accumulator records (acc_stride(D) floats each) of this kind
+  int* phase;            // accumulator phase of this kind (0..2)
+  int* done;             // CUDA blocks finished (the last one advances the phase)
   float* out;            // flux in schedule layout or nullptr
   const int32_t* fold_rec;  // every copy of a shared vertex: its record and shared id
   const int32_t* fold_sid;
@@ -96,9 +97,9 @@ const void* flux_tma_kernel_ptr(int D, bool adjoint);
 cudaError_t flux_step(const FluxArgs& a, int D, cudaStream_t st);
 // read-only-cache variant (no staging); needs max_np <= 4096
 cudaError_t flux_step_ldg(const FluxArgs& a, int D, cudaStream_t st);
-// shared-vertex fold after an edge kernel: every copy r of shared vertex h
-// becomes x_out[r] = x_in[r] + tau * acc[h]; out[r] (if not null) = acc[h];
-// the other accumulator buffer is cleared and the phase flips
+// finish of a pending state: every copy r of shared vertex h becomes
+// x_out[r] = x_in[r] + tau * prev[h]; out[r] (if not null) = prev[h]
+// (flux_common.cuh: the accumulator rotation)
 cudaError_t bnd_update(const FluxArgs& a, int D, float* x_out, const float* x_in, float* out,
                        cudaStream_t st);
 cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, cudaStream_t st);

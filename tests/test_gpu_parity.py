@@ -475,3 +475,92 @@ def test_autotuner_pick_runs_against_oracle():
     src = np.concatenate([g[1] + o for g, o in zip(graphs, offs)]).astype(np.int32)
     dst = np.concatenate([g[2] + o for g, o in zip(graphs, offs)]).astype(np.int32)
     _flux_fwd_adj_vs_oracle(B, src, dst, sum(sizes), "autotuned batch", (tuned["stages"],))
+
+
+# ------------------------------------------------------------- pending copies
+
+@pytest.mark.parametrize("stages,cache", [(3, 0), (0, 0), (3, 1), (2, 0)])
+def test_pending_steps_match_oracle(small_mesh, stages, cache):
+    """Pending steps (shared copies one step behind), complete steps and finishes mixed."""
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 128)
+    S.set_pipeline(stages)
+    S.set_cache(cache)
+    x0 = W.flux_state(n, 5, 12)
+    w = W.flux_weights(src.size, 12)
+    xl = torch.zeros(S.layout_floats(5), device="cuda")
+    wl = torch.zeros(S.weights_floats(), device="cuda")
+    S.layout_in(cuda(x0), xl)
+    S.weights_in(cuda(w), wl)
+    tau = 1e-2
+    for pending in (True, True, True, False, True, True):
+        S.step(5, xl, xl, wl, None, tau, pending=pending)
+    S.finish(5, xl, tau)
+    S.finish(5, xl, tau)  # finishing a finished state changes nothing
+    x = torch.zeros(5, n, device="cuda")
+    S.layout_out(xl, x)
+    xT, _ = O.flux_steps(src, dst, x0, w, 6, tau)
+    check_state(x, xT, x0, 6, "x")
+    # out of place pending steps, then a complete one with the flux
+    x2 = torch.zeros_like(xl)
+    S.step(5, xl, x2, wl, None, tau, pending=True)
+    out = torch.zeros_like(xl)
+    S.step(5, x2, xl, wl, out, tau)
+    xo = torch.zeros(5, n, device="cuda")
+    fo = torch.zeros(5, n, device="cuda")
+    S.layout_out(xl, xo)
+    S.layout_out(out, fo)
+    xT2, fT2 = O.flux_steps(src, dst, x0, w, 8, tau)
+    check_state(xo, xT2, x0, 8, "x after 8")
+    check_field(fo, fT2, "out of step 8")
+    assert S.check_errors() == 0
+
+
+@pytest.mark.parametrize("stages", [0, 3])
+def test_pending_adjoint_steps_match_oracle(small_mesh, stages):
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 256)
+    S.set_pipeline(stages)
+    x0 = W.flux_state(n, 5, 13)
+    w = W.flux_weights(src.size, 13)
+    g = W.loss_weights(n, 5, 4)
+    tau, T = 1e-2, 4
+    wl = torch.zeros(S.weights_floats(), device="cuda")
+    S.weights_in(cuda(w), wl)
+    states = [torch.zeros(S.layout_floats(5), device="cuda") for _ in range(T)]
+    S.layout_in(cuda(x0), states[0])
+    for t in range(T - 1):
+        S.step(5, states[t], states[t + 1], wl, None, tau)
+    lam = torch.zeros_like(states[0])
+    S.layout_in(cuda(g), lam)
+    gwl = torch.zeros_like(wl)
+    for t in range(T - 1, -1, -1):
+        S.adjoint_step(5, states[t], wl, lam, gwl, tau, pending=(t % 2 == 1))
+    S.adjoint_finish(5, lam, tau)
+    dx = torch.zeros(5, n, device="cuda")
+    S.layout_out(lam, dx)
+    dw = torch.zeros(src.size, device="cuda")
+    S.weights_out_add(gwl, dw)
+    dx_ref, dw_ref = O.flux_adjoint(src, dst, x0, w, T, tau, g)
+    check_state(dx, dx_ref, g, T, "dx0")
+    check_field(dw, dw_ref, "dw")
+
+
+def test_new_state_discards_pending_sums(small_mesh):
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 256)
+    x0 = W.flux_state(n, 5, 14)
+    x1 = W.flux_state(n, 5, 15)
+    w = W.flux_weights(src.size, 14)
+    wl = torch.zeros(S.weights_floats(), device="cuda")
+    S.weights_in(cuda(w), wl)
+    xa = torch.zeros(S.layout_floats(5), device="cuda")
+    S.layout_in(cuda(x0), xa)
+    S.step(5, xa, xa, wl, None, 1e-2, pending=True)  # left pending on purpose
+    xb = torch.zeros_like(xa)
+    S.layout_in(cuda(x1), xb)  # a new state: the pending sums must not reach it
+    S.step(5, xb, xb, wl, None, 1e-2)
+    x = torch.zeros(5, n, device="cuda")
+    S.layout_out(xb, x)
+    ref, _ = O.flux_steps(src, dst, x1, w, 1, 1e-2)
+    check_state(x, ref, x1, 1, "x")
