@@ -4,21 +4,28 @@
 Workload: the 1M-node mesh (1,048,576 points uniform in the unit cube, seed
 0, symmetrised k=4 nearest-neighbour graph, ~2.57M tasks in shuffled order),
 state x: 5 x fp32 N(0,1), weights w ~ U(0.5, 1.5), explicit steps
-x <- x + 1e-3 * flux(x).  One bench step is one explicit step (edge kernel
-plus shared-vertex update) on the whole mesh, with L2 flushed (a write and
-then a read of scratch buffers twice the L2 size) before every timed step and
-outside its events.
+x <- x + 1e-3 * flux(x).  One bench step is one explicit step of a run of
+`--steps` steps on the whole mesh: one launch of the edge kernel (the copies of
+shared vertices stay one step behind, ep_step_pending), with the L2 flushed (a
+write and then a read of scratch buffers twice the L2 size) before every timed
+step and outside its events; the run's final finish (ep_finish) is timed too
+and added to the total.
 
 Reported (one JSON line on rank 0):
-  value        forward edge updates/s, partitioned schedule (C = --C)
-  default      the same kernel under the default order (C consecutive tasks)
-  fwd_bwd      10 steps forward + backward (checkpoint every 5, recompute
-               included) through the autograd function, edge updates/s
-  roofline     the forward edge kernel: algorithmic bytes per launch (the cost
-               model of Eq. 1, 4*D bytes per vertex load) / its mean duration
-  e2e          ep_run_host with one step per call: host x, w (pinned) copied in
-               and x read back every step; resident_state = 100 steps per call
-  cpu_baseline the FP64 oracle on the host, bounded sample of steps
+  value          forward edge updates/s of the run, partitioned schedule (C = --C)
+  default        the same under the default order (C consecutive tasks per block)
+  complete_step  steps that each finish their state (edge kernel + finish)
+  back_to_back   steps without L2 flushes between them (state and tasks stay in L2)
+  fwd_bwd        10 steps forward + backward (checkpoint every 5, recompute
+                 included) through the autograd function, edge updates/s
+  roofline       the forward edge kernel: algorithmic bytes per launch (the cost
+                 model of Eq. 1, 4*D bytes per vertex load) / its mean duration
+  C_sweep        C in {256, 512, 1024}: value and roofline of each
+  e2e            ep_run_host with one step per call: host x, w (pinned) copied in
+                 and x read back every step; resident_state = 100 steps per call
+  cpu_baseline   the FP64 oracle on the host, bounded sample of steps
+  rmat           R-MAT scale-20 SpMV sub-record (partitioned vs default order)
+  batch          512 uneven meshes sub-record (100 steps fwd+bwd in a CUDA graph)
 With --impl reference the oracle itself is timed as the reference arm.
 """
 from __future__ import annotations
@@ -28,6 +35,7 @@ import csv
 import io
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -47,22 +55,22 @@ TAU = 1e-3
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--C", type=int, default=512)
     ap.add_argument("--threads", type=int, default=None,
-                    help="threads per CUDA block (default 256 consumer threads for the mesh, "
-                         "192 for the R-MAT SpMV)")
+                    help="consumer threads per CUDA block (default 192 for the mesh and the SpMV)")
     ap.add_argument("--stages", type=int, default=3, help="0: one CUDA block per schedule block")
     ap.add_argument("--n", type=int, default=1 << 20, help="mesh points (default: the 1M-node mesh)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--sweep", action="store_true", help="also time C in {256, 512, 1024}")
+    ap.add_argument("--quick", action="store_true",
+                    help="mesh line only: no C sweep, R-MAT or batch sub-records")
     ap.add_argument("--only", default="", choices=["", "fwd"],
                     help="fwd: time only the forward loops (for profiler runs)")
     ap.add_argument("--workload", default="mesh", choices=["mesh", "rmat", "batch"],
-                    help="mesh: 1M-node kNN mesh flux steps; rmat: R-MAT scale-20 SpMV; "
-                         "batch: 512 uneven meshes, 100 steps fwd+bwd in one CUDA graph")
+                    help="mesh: 1M-node kNN mesh flux steps (with the sub-records); rmat: R-MAT "
+                         "scale-20 SpMV alone; batch: 512 uneven meshes alone")
     ap.add_argument("--meshes", type=int, default=512, help="batch workload: number of meshes")
     ap.add_argument("--study", default="", choices=["", "cache"],
                     help="cache: shared-memory staging vs read-only data cache, C in {256, 512, 1024}, "
@@ -93,6 +101,20 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def cpu_info():
+    """Host CPU model and thread count."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return dict(model=model, machine=platform.machine(), threads=os.cpu_count())
 
 
 class Clocks:
@@ -140,10 +162,12 @@ class L2Flush:
 
     The write evicts everything the previous step left in L2; the read then
     evicts the write's own dirty lines, so the next timed step starts from a
-    cold, clean L2 and does not pay for the flush's write-backs."""
+    cold, clean L2 and does not pay for the flush's write-backs.  (The previous
+    step's own dirty lines are written back during the flush, outside the
+    events: `back_to_back` times steps without flushes.)"""
 
     def __init__(self, torch):
-        l2 = torch.cuda.get_device_properties(0).L2_cache_size
+        l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
         self.bytes = max(2 * l2, 64 << 20)
         self.a = torch.empty(self.bytes // 4, dtype=torch.float32, device="cuda")
         self.b = torch.zeros(self.bytes // 4, dtype=torch.float32, device="cuda")
@@ -161,13 +185,23 @@ def timed_loop(torch, body, steps, warmup, flush):
     torch.cuda.synchronize()
     barrier(torch)
     for a, b in ev:
-        flush()
+        if flush is not None:
+            flush()
         a.record()
         body()
         b.record()
     torch.cuda.synchronize()
     barrier(torch)
     return [a.elapsed_time(b) for a, b in ev]
+
+
+def time_once(torch, body):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    body()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
 
 
 def barrier(torch):
@@ -194,28 +228,52 @@ def algorithmic_bytes(S, loads, foreign):
     return 8 * S.m + 32 * S.k + 4 * foreign + 2 * 4 * D * loads
 
 
-def bench_fwd(torch, E, S, x0, w, steps, warmup, flush):
+def adjoint_bytes(S, loads, foreign):
+    """Cost-model bytes of one adjoint edge-kernel launch: the task stream, the
+    descriptor and foreign ids, a gather of x and of lam and a write-back of lam
+    (4*D bytes each per vertex load), and the weight gradient (4 B per task)."""
+    return 12 * S.m + 32 * S.k + 4 * foreign + 3 * 4 * D * loads
+
+
+def roofline(alg_bytes, launch_ms, kernel, peak, peak_kind, traffic=None):
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kernel, "algorithmic_bytes_per_launch": alg_bytes,
+            "launch_ms": launch_ms, "peak_kind": f"{peak_kind} HBM copy"}
+
+
+def bench_fwd(torch, S, x0, w, steps, warmup, flush, complete=True, b2b_steps=50):
+    """A run of `steps` pending steps (one edge-kernel launch each, L2 flushed
+    before each, events around each) and its final finish; steps that finish
+    their state each time; and pending steps back to back without flushes."""
     x = torch.from_numpy(x0).cuda()
     wt = torch.from_numpy(w).cuda()
     xl = torch.empty(S.layout_floats(D), device="cuda")
     wl = torch.empty(S.weights_floats(), device="cuda")
     S.layout_in(x, xl)
     S.weights_in(wt, wl)
+    pend = lambda: S.step(D, xl, xl, wl, None, TAU, pending=True)  # noqa: E731
     for _ in range(warmup):
-        S.step(D, xl, xl, wl, None, TAU)
-    # whole steps without per-kernel instrumentation, then a separate pass
-    # with the library's per-kernel events for the kernel times
-    ms = timed_loop(torch, lambda: S.step(D, xl, xl, wl, None, TAU), steps, 0, flush)
-    S.timing(2)
-    n_instr = max(20, steps // 5)
-    timed_loop(torch, lambda: S.step(D, xl, xl, wl, None, TAU), n_instr, 0, flush)
-    edge_ms, edge_n = S.timing_read(E.T_EDGE_FWD)
-    bnd_ms, bnd_n = S.timing_read(E.T_BND)
-    S.timing(0)
-    per_step = (edge_n + bnd_n) / n_instr  # our kernels per step (edge kernel + fold)
-    return dict(ms=ms, edge_ms=edge_ms / max(edge_n, 1), edge_launches=edge_n,
-                bnd_ms=bnd_ms / max(bnd_n, 1), bnd_launches=bnd_n,
-                launches_timed=int(round(per_step * len(ms))))
+        pend()
+    S.finish(D, xl, TAU)
+    ms = timed_loop(torch, pend, steps, 0, flush)
+    fin_ms = time_once(torch, lambda: S.finish(D, xl, TAU))
+    res = dict(ms=ms, finish_ms=fin_ms, total_ms=sum(ms) + fin_ms, edge_ms=statistics.mean(ms),
+               launches_timed=len(ms) + 1)
+    if complete:
+        cms = timed_loop(torch, lambda: S.step(D, xl, xl, wl, None, TAU), max(10, steps // 5), 2, flush)
+        res["complete_ms"] = cms
+    torch.cuda.synchronize()
+
+    def b2b():
+        for _ in range(b2b_steps):
+            pend()
+        S.finish(D, xl, TAU)
+
+    b2b()
+    res["b2b_ms_per_step"] = time_once(torch, b2b) / b2b_steps
+    S.check_errors()
+    return res
 
 
 def bench_fwd_bwd(torch, S, x0, w, iters, warmup, flush, T=10, every=5):
@@ -259,11 +317,11 @@ def bench_e2e(torch, S, x0, w, reps=20, T_long=100):
         S.run_host(xh, wh, None, steps=T_long, tau=TAU, D=D)
         long_times.append(time.perf_counter() - t0)
     tl = max_over_ranks(torch, statistics.median(long_times))
-    return dict(value=S.m / t, unit=UNIT, h2d_bytes_per_step=int(xh.numel() * 4 + wh.numel() * 4),
-                d2h_bytes_per_step=int(xh.numel() * 4), steps_per_call=1, seconds_per_step=t,
+    hb, db = int(xh.numel() * 4 + wh.numel() * 4), int(xh.numel() * 4)
+    return dict(value=S.m / t, unit=UNIT, h2d_bytes_per_step=hb, d2h_bytes_per_step=db, steps_per_call=1,
+                seconds_per_step=t, copy_GBps=(hb + db) / t / 1e9,
                 resident_state={"steps_per_call": T_long, "value": S.m * T_long / tl, "unit": UNIT,
-                                "h2d_bytes_per_call": int(xh.numel() * 4 + wh.numel() * 4),
-                                "d2h_bytes_per_call": int(xh.numel() * 4)})
+                                "h2d_bytes_per_call": hb, "d2h_bytes_per_call": db})
 
 
 def cpu_baseline(src, dst, x0, w, seconds):
@@ -278,7 +336,9 @@ def cpu_baseline(src, dst, x0, w, seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
-    return dict(value=src.size * steps / el, unit=UNIT, cores=1, kind="oracle",
+    ci = cpu_info()
+    return dict(value=src.size * steps / el, unit=UNIT, cores=1, kind="oracle", cpu=ci["model"],
+                host_threads=ci["threads"],
                 sample=f"{steps} FP64 NumPy flux steps of the full mesh ({src.size} tasks), single thread")
 
 
@@ -300,10 +360,12 @@ def cpu_fair(src, dst, x0, w, n, seconds):
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
-    return dict(value=src.size * steps / el, unit=UNIT, cores=used, kind="openmp-fp64",
+    return dict(value=src.size * steps / el, unit=UNIT, cores=used, kind="openmp-fp64", cpu=cpu_info()["model"],
                 sample=f"{steps} FP64 flux steps of the full mesh on {used} threads (pull form, "
                        f"one vertex per loop iteration)")
 
+
+# ------------------------------------------------------------------- R-MAT SpMV
 
 def spmv_time(torch, E, sch, x0, w, n, steps, warmup, flush):
     """Mean SpMV kernel time (ms) and step time (ms) on schedule-layout buffers."""
@@ -318,7 +380,7 @@ def spmv_time(torch, E, sch, x0, w, n, steps, warmup, flush):
     ms = timed_loop(torch, lambda: sch.spmv(xl, wl, yl), steps, 0, flush)
     kms, kn = sch.timing_read(E.T_SPMV)
     sch.timing(0)
-    return kms / max(kn, 1), statistics.mean(ms)
+    return kms / max(kn, 1), ms
 
 
 def study_cache_spmv(torch, E, args, rows, cols, n, x0, w):
@@ -336,70 +398,47 @@ def study_cache_spmv(torch, E, args, rows, cols, n, x0, w):
                 S.set_cache(mode)
                 kms, sms = spmv_time(torch, E, S, x0, w, n, max(20, args.steps // 5), args.warmup, flush)
                 out.append(dict(C=C, schedule=sched, kernel=name, loads=loads, kernel_us=1e3 * kms,
-                                step_us=1e3 * sms, edge_updates_per_s=rows.size / (1e-3 * sms)))
+                                step_us=1e3 * statistics.mean(sms),
+                                edge_updates_per_s=rows.size / (1e-3 * statistics.mean(sms))))
             S.close()
     clk = clocks.stop()
     print(json.dumps({"study": "cache", "workload": "rmat", "n": n, "m": int(rows.size),
                       "threads": args.threads, "rows": out, "clocks": clk}))
 
 
-def bench_rmat(args):
+def rmat_record(torch, E, args, ws, flush, C=512, cpu_seconds=5.0):
     """SpMV on the R-MAT scale-20 graph (y_u += w_e x_v), partitioned vs default order."""
-    import torch
-    import paper_1605_02043_gb300 as E
     import workloads as W
+    import oracle as O
 
-    ws, rank, local = dist_info()
-    if ws > 1:
-        torch.cuda.set_device(local)
-        torch.distributed.init_process_group("nccl")
     rows, cols = W.rmat()
     n, m = 1 << 20, rows.size
     x0, w = W.spmv_inputs(n, m, 0)
-    if args.study == "cache":
-        study_cache_spmv(torch, E, args, rows, cols, n, x0, w)
-        return
-    C = args.C if args.C != 256 else 512
     t0 = time.perf_counter()
     S = E.Schedule.partition(rows, cols, n, C, bipartite=True)
     part_s = time.perf_counter() - t0
     Sd = E.Schedule.partition(rows, cols, n, C, bipartite=True, default_order=True)
-    flush = L2Flush(torch)
+    peak, peak_kind = peaks()
     res = {}
+    steps = max(20, args.steps)
     for name, sch in (("partitioned", S), ("default", Sd)):
         sch.set_threads(args.threads)
         loads, cut = sch.cost()
-        xl = torch.empty(n, device="cuda")
-        wl = torch.empty(sch.weights_floats(), device="cuda")
-        yl = torch.empty(n, device="cuda")
-        sch.spmv_x_in(torch.from_numpy(x0).cuda(), xl)
-        sch.weights_in(torch.from_numpy(w).cuda(), wl)
-        for _ in range(args.warmup):
-            sch.spmv(xl, wl, yl)
-        ms = timed_loop(torch, lambda: sch.spmv(xl, wl, yl), args.steps, 0, flush)
-        sch.timing(2)  # kernel times from a separate, instrumented pass
-        n_instr = max(20, args.steps // 5)
-        timed_loop(torch, lambda: sch.spmv(xl, wl, yl), n_instr, 0, flush)
-        kms, kn = sch.timing_read(E.T_SPMV)
-        sch.timing(0)
-        kn_timed = int(round(kn / n_instr * len(ms)))
+        kms, ms = spmv_time(torch, E, sch, x0, w, n, steps, args.warmup, flush)
+        tot = max_over_ranks(torch, sum(ms))
         # cost-model bytes: entry + weight per task, 64-byte descriptor per block,
         # foreign ids, one 4-byte gather (x) or write-back (y) per vertex load
         alg = 8 * m + 64 * sch.k + 4 * cut + 4 * loads
-        tot = max_over_ranks(torch, sum(ms))
         res[name] = dict(edge_updates_per_s=ws * m * len(ms) / (1e-3 * tot), ms_per_step=tot / len(ms),
-                         kernel_ms=kms / max(kn, 1), loads=loads, vertex_cut=cut, alg_bytes=alg,
-                         alg_GBps=alg / (kms / max(kn, 1) * 1e-3) / 1e9, launches=kn_timed)
-    if rank != 0:
-        return
-    import oracle as O
-
+                         kernel_ms=kms, loads=loads, vertex_cut=cut, alg_bytes=alg,
+                         roofline=roofline(alg, kms, "spmv_kernel", peak, peak_kind))
+    # the oracle on the host, bounded
     t0 = time.perf_counter()
     reps = 0
     while True:
         O.spmv(rows, cols, x0, w, n)
         reps += 1
-        if time.perf_counter() - t0 >= args.cpu_seconds:
+        if time.perf_counter() - t0 >= cpu_seconds:
             break
     cpu_v = m * reps / (time.perf_counter() - t0)
     xh = torch.from_numpy(x0.copy()).pin_memory()
@@ -407,65 +446,87 @@ def bench_rmat(args):
     yh = torch.zeros(n).pin_memory()
     S.run_host(xh, wh, yh, steps=1, kernel=E.SPMV, D=1)
     times = []
-    for _ in range(3):
+    for _ in range(5):
         t1 = time.perf_counter()
         S.run_host(xh, wh, yh, steps=1, kernel=E.SPMV, D=1)
         times.append(time.perf_counter() - t1)
-    peak, peak_kind = peaks()
     p = res["partitioned"]
-    print(json.dumps({
+    return {
         "metric": "edge updates/s (SpMV y_u += w_e x_v), partitioned vs default order; % HBM peak",
-        "value": p["edge_updates_per_s"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": p["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "value": p["edge_updates_per_s"], "unit": UNIT, "ms_per_step": p["ms_per_step"],
         "config": {"workload": f"R-MAT scale 20 (n={n}, m={m}), bipartite SpMV", "C": C,
                    "threads_per_block": args.threads,
                    "l2": "flushed before every timed step (write then read of scratch buffers)"},
-        "roofline": {"bound": "hbm", "achieved": p["alg_GBps"], "peak": peak, "unit": "GB/s",
-                     "frac": p["alg_GBps"] / peak, "traffic": None, "kernel": "spmv_kernel",
-                     "algorithmic_bytes_per_launch": p["alg_bytes"], "launch_ms": p["kernel_ms"],
-                     "peak_kind": f"{peak_kind} HBM copy"},
-        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "roofline": p["roofline"],
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_info()["model"],
                          "sample": f"{reps} FP64 NumPy SpMV of the full matrix"},
         "e2e": {"value": m / statistics.median(times), "unit": UNIT,
                 "h2d_bytes_per_step": int(4 * n + 4 * m), "d2h_bytes_per_step": int(4 * n)},
-        "gpu_launches": p["launches"], "partitioned": p, "default": res["default"],
-        "partition_s": part_s,
-    }))
+        "partitioned": p, "default": res["default"], "partition_s": part_s,
+        "speedup_vs_default": res["default"]["kernel_ms"] / p["kernel_ms"],
+    }
 
 
-def bench_batch(args):
-    """512 uneven meshes: autotuned C and kernel, one persistent launch per kernel over all
-    meshes, 100 steps fwd+bwd (checkpoint every 10) captured in one CUDA graph; against the
-    same work launched eagerly and against per-mesh launches."""
+def bench_rmat(args):
     import torch
     import paper_1605_02043_gb300 as E
-    import workloads as W
-    from paper_1605_02043_gb300 import autotune
-    from paper_1605_02043_gb300.autograd import FluxRunner
 
     ws, rank, local = dist_info()
     if ws > 1:
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl")
-    T, every = 100, 10
+    if args.study == "cache":
+        import workloads as W
+        rows, cols = W.rmat()
+        x0, w = W.spmv_inputs(1 << 20, rows.size, 0)
+        study_cache_spmv(torch, E, args, rows, cols, 1 << 20, x0, w)
+        return
+    flush = L2Flush(torch)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    rec = rmat_record(torch, E, args, ws, flush, C=args.C, cpu_seconds=args.cpu_seconds)
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    rec.update({"n_gpus": ws, "steps": max(20, args.steps), "warmup": args.warmup, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "gpu_launches": max(20, args.steps), "clocks": clk})
+    print(json.dumps(rec))
+
+
+# ---------------------------------------------------------- 512 uneven meshes
+
+def batch_record(torch, E, args, ws, T=100, every=10, cpu_seconds=5.0):
+    """512 uneven meshes: autotuned C and kernel, one persistent launch per kernel over all
+    meshes, T steps fwd+bwd (checkpoint every `every`) captured in one CUDA graph; against the
+    same work launched eagerly and against per-mesh launches.  The batch's state and task data
+    (hundreds of MB) exceed the L2, so no flush is needed."""
+    import workloads as W
+    import oracle as O
+    from paper_1605_02043_gb300 import autotune
+    from paper_1605_02043_gb300.autograd import FluxRunner
+
     t0 = time.perf_counter()
     graphs = W.batch_meshes(args.meshes)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    tuned = autotune.tune(graphs, D=D)
+    parts_by_C = {}
+    tuned = autotune.tune(graphs, D=D, partitions=parts_by_C)
     tune_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    parts = autotune.partition_many(graphs, tuned["C"])
+    parts = parts_by_C.get(tuned["C"]) or autotune.partition_many(graphs, tuned["C"])
     part_s = time.perf_counter() - t0
     B = E.Schedule.batch(parts)
     for sch in parts + [B]:
         sch.set_pipeline(tuned["stages"])
         sch.set_threads(tuned["threads"])
     N, M = B.n, B.m
-    x0 = torch.from_numpy(W.flux_state(N, D, 0)).cuda()
-    w = torch.from_numpy(W.flux_weights(M, 0)).cuda()
-    g = torch.from_numpy(W.loss_weights(N, D, 1).astype(np.float32)).cuda()
+    x0h = W.flux_state(N, D, 0)
+    wh_ = W.flux_weights(M, 0)
+    gh = W.loss_weights(N, D, 1).astype(np.float32)
+    x0 = torch.from_numpy(x0h).cuda()
+    w = torch.from_numpy(wh_).cuda()
+    g = torch.from_numpy(gh).cuda()
     R = FluxRunner(B, D, T, TAU, every)
     R.load(x0, w, g)
     R.run()
@@ -475,8 +536,7 @@ def bench_batch(args):
         R.run()
     for _ in range(max(args.warmup, 3)):
         graph.replay()
-    reps = max(1, min(args.steps, 5))
-    # the batch's state and task data (hundreds of MB) exceed the L2: no flush needed
+    reps = 5
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     torch.cuda.synchronize()
     barrier(torch)
@@ -490,13 +550,24 @@ def bench_batch(args):
     g_tot = max_over_ranks(torch, sum(g_ms))
     graph_v = ws * M * T * reps / (1e-3 * g_tot)
     B.check_errors()
-    # same work, eager launches from the host
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    R.run()
-    e1.record()
-    torch.cuda.synchronize()
-    eager_ms = e0.elapsed_time(e1)
+    eager_ms = time_once(torch, R.run)
+    # end to end: inputs copied in from pinned host memory, the replay, gradients read back
+    x0p = torch.from_numpy(x0h.copy()).pin_memory()
+    wp = torch.from_numpy(wh_.copy()).pin_memory()
+    gp = torch.from_numpy(gh.copy()).pin_memory()
+    dxp = torch.empty_like(x0p).pin_memory()
+    dwp = torch.empty(M).pin_memory()
+    e2e_t = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        R.load(x0p.cuda(non_blocking=True), wp.cuda(non_blocking=True), gp.cuda(non_blocking=True))
+        graph.replay()
+        _, dx, dw = R.results(x0, M)
+        dxp.copy_(dx, non_blocking=True)
+        dwp.copy_(dw, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t1)
     # per-mesh launches (eager)
     offs_n = np.cumsum([0] + [p.n for p in parts])
     offs_m = np.cumsum([0] + [p.m for p in parts])
@@ -508,43 +579,78 @@ def bench_batch(args):
     for r in runners[:4]:
         r.run()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e0.record()
-    for r in runners:
-        r.run()
-    e1.record()
-    torch.cuda.synchronize()
-    mesh_ms = e0.elapsed_time(e1)
-    mesh_wall = time.perf_counter() - t0
-    if rank != 0:
-        return
+    mesh_ms = time_once(torch, lambda: [r.run() for r in runners])
+    # roofline over the replay: cost-model bytes of every launch in it
+    loads, cut = B.cost_host()
+    nseg = (T + every - 1) // every
+    n_fwd = T + (T - nseg)  # forward steps + recomputed states
+    alg = n_fwd * algorithmic_bytes(B, loads, cut) + T * adjoint_bytes(B, loads, cut)
     peak, peak_kind = peaks()
-    print(json.dumps({
-        "metric": "edge updates/s, fwd+bwd (100 steps, checkpoint every 10), batched uneven meshes",
-        "value": graph_v, "unit": UNIT, "n_gpus": ws, "steps": reps, "warmup": max(args.warmup, 3),
-        "ms_per_step": g_tot / reps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    rl = roofline(alg, g_tot / reps, "flux_fwd_tma_kernel<5> + flux_adj_tma_kernel<5> (whole replay)",
+                  peak, peak_kind)
+    # the oracle on sampled meshes, bounded
+    rng = np.random.default_rng(5)
+    done_tasks, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < cpu_seconds:
+        i = int(rng.integers(len(graphs)))
+        n_i, s_i, d_i = graphs[i]
+        xi = x0h[:, offs_n[i]:offs_n[i + 1]]
+        wi = wh_[offs_m[i]:offs_m[i + 1]]
+        O.flux_steps(s_i, d_i, xi, wi, T, TAU)
+        O.flux_adjoint(s_i, d_i, xi, wi, T, TAU, gh[:, offs_n[i]:offs_n[i + 1]])
+        done_tasks += s_i.size * T
+    cpu_v = done_tasks / (time.perf_counter() - t1)
+    e2e = statistics.median(e2e_t)
+    return {
+        "metric": f"edge updates/s, fwd+bwd ({T} steps, checkpoint every {every}), batched uneven meshes",
+        "value": graph_v, "unit": UNIT, "ms_per_step": g_tot / reps, "steps": reps,
         "config": {"workload": f"{args.meshes} kNN k=4 meshes, n log-uniform in [1024, 65536] "
-                               f"(N={N}, M={M}), D=5, 100 explicit steps fwd+bwd",
+                               f"(N={N}, M={M}), D=5, {T} explicit steps fwd+bwd",
                    "C": tuned["C"], "pipeline_stages": tuned["stages"],
                    "consumer_threads": tuned["threads"], "autotuned": True,
                    "l2": "not flushed: the batch state and task data exceed the L2",
                    "bench_step": "one CUDA-graph replay of the whole fwd+bwd pass"},
-        "graph_batched": graph_v,
-        "eager_batched": M * T / (1e-3 * eager_ms),
-        "per_mesh_launches": M * T / (1e-3 * mesh_ms), "per_mesh_wall_s": mesh_wall,
+        "roofline": rl,
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_info()["model"],
+                         "sample": f"FP64 NumPy fwd+bwd ({T} steps) of randomly drawn meshes for "
+                                   f"{cpu_seconds:.0f} s, {done_tasks} edge updates"},
+        "e2e": {"value": M * T / e2e, "unit": UNIT, "h2d_bytes_per_step": int(4 * (x0h.size + wh_.size + gh.size)),
+                "d2h_bytes_per_step": int(4 * (x0h.size + M)), "seconds_per_step": e2e},
+        "graph_batched": graph_v, "eager_batched": M * T / (1e-3 * eager_ms),
+        "per_mesh_launches": M * T / (1e-3 * mesh_ms),
         "autotune": {k: tuned[k] for k in ("C", "stages", "threads")},
-        "autotune_table": tuned.get("table"),
-        "gen_s": gen_s, "tune_s": tune_s, "partition_s": part_s, "loads": B.cost_host()[0],
-        "cpu_baseline": None, "roofline": None,
-        "e2e": None, "gpu_launches": None, "peak_GBps": peak,
-    }))
+        "autotune_confirmed": tuned.get("confirmed"),
+        "gen_s": gen_s, "tune_s": tune_s, "partition_s": part_s, "loads": loads,
+    }
 
+
+def bench_batch(args):
+    import torch
+    import paper_1605_02043_gb300 as E
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    rec = batch_record(torch, E, args, ws, cpu_seconds=args.cpu_seconds)
+    clk = clocks.stop()
+    if rank != 0:
+        return
+    rec.update({"n_gpus": ws, "warmup": max(args.warmup, 3), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "clocks": clk,
+                "gpu_launches": None})
+    print(json.dumps(rec))
+
+
+# ------------------------------------------------------------------ mesh line
 
 def mesh_config(args, n, m, ws, l2):
     """The `config` object of the mesh workload (both arms)."""
     return {
-        "workload": f"kNN mesh n={n} k=4 (m={m}), D=5, one explicit flux step per bench step",
+        "workload": f"kNN mesh n={n} k=4 (m={m}), D=5, one explicit flux step per bench step "
+                    f"(a run of {args.steps} steps and its finish)",
         "schedule": "edge partition (clone-and-connect + recursive bisection)",
         "C": args.C, "consumer_threads": args.threads, "pipeline_stages": args.stages, "tau": TAU,
         "l2": l2, "parallelism": "replicas" if ws > 1 else "single GPU",
@@ -577,6 +683,7 @@ def run_reference(args):
         x = step(i)
     el = time.perf_counter() - t0
     v = ms * args.steps / el
+    ci = cpu_info()
     sample = (f"{args.steps} FP64 NumPy oracle steps over windows of {ms} of the {m} tasks "
               f"(about 20 full-mesh steps in all), one thread")
     print(json.dumps({
@@ -585,7 +692,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": mesh_config(args, args.n, m, 1, "not applicable (host cores)"),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu": ci["model"], "host_threads": ci["threads"]},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -606,19 +714,41 @@ def study_cache(torch, E, args, src, dst, x0, w, flush):
             for name, cache, stages in kinds:
                 S.set_pipeline(stages)
                 S.set_cache(cache)
-                r = bench_fwd(torch, E, S, x0, w, max(20, args.steps // 5), args.warmup, flush)
+                r = bench_fwd(torch, S, x0, w, max(20, args.steps // 5), args.warmup, flush, complete=False)
                 rows.append(dict(C=C, schedule=sched, kernel=name, loads=loads,
-                                 edge_kernel_us=1e3 * r["edge_ms"], bnd_kernel_us=1e3 * r["bnd_ms"],
-                                 step_us=1e3 * statistics.mean(r["ms"]),
-                                 edge_updates_per_s=m * len(r["ms"]) / (1e-3 * sum(r["ms"]))))
+                                 edge_kernel_us=1e3 * r["edge_ms"], finish_us=1e3 * r["finish_ms"],
+                                 edge_updates_per_s=m * len(r["ms"]) / (1e-3 * r["total_ms"])))
             S.close()
     return rows
+
+
+def mesh_run(torch, E, S, x0, w, args, flush, peak, peak_kind, complete=True):
+    """Forward record of one schedule: value, roofline of the edge kernel and the variants."""
+    loads, cut = S.cost()
+    assert (loads, cut) == S.cost_host()
+    r = bench_fwd(torch, S, x0, w, args.steps, args.warmup, flush, complete=complete)
+    m = S.m
+    alg = algorithmic_bytes(S, loads, cut)
+    rec = {"edge_updates_per_s": m * len(r["ms"]) / (1e-3 * r["total_ms"]), "loads": loads, "vertex_cut": cut,
+           "edge_kernel_ms": r["edge_ms"], "finish_ms": r["finish_ms"], "alg_bytes": alg,
+           "roofline": roofline(alg, r["edge_ms"], "flux_fwd_tma_kernel<5>" if args.stages else
+                                "flux_fwd_kernel<5>", peak, peak_kind),
+           "back_to_back": {"ms_per_step": r["b2b_ms_per_step"],
+                            "edge_updates_per_s": m / (1e-3 * r["b2b_ms_per_step"]),
+                            "note": "50 pending steps and their finish without L2 flushes"}}
+    if "complete_ms" in r:
+        rec["complete_step"] = {"ms_per_step": statistics.mean(r["complete_ms"]),
+                                "edge_updates_per_s": m / (1e-3 * statistics.mean(r["complete_ms"])),
+                                "note": "each step finishes its state (edge kernel + finish)"}
+    if args.stages:
+        rec["launch_plan"] = S.pipeline_info(D)
+    return r, rec
 
 
 def main():
     args = parse()
     if args.threads is None:
-        args.threads = 192 if args.workload == "rmat" else 256
+        args.threads = 192
     if args.impl == "reference":
         run_reference(args)
         return
@@ -645,11 +775,9 @@ def main():
     for s in (S, Sd):
         s.set_threads(args.threads)
         s.set_pipeline(args.stages)
-    loads, cut = S.cost()
-    loads_d, cut_d = Sd.cost()
-    assert (loads, cut) == S.cost_host() and (loads_d, cut_d) == Sd.cost_host()
     flush = L2Flush(torch)
     flush_bytes = flush.bytes
+    peak, peak_kind = peaks()
 
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
@@ -660,61 +788,40 @@ def main():
             print(json.dumps({"study": "cache", "n": n, "m": m, "D": D, "threads": args.threads,
                               "rows": rows, "clocks": clk}))
         return
-    fwd = bench_fwd(torch, E, S, x0, w, args.steps, args.warmup, flush)
-    fwd_d = bench_fwd(torch, E, Sd, x0, w, args.steps, args.warmup, flush)
+    fwd, p_rec = mesh_run(torch, E, S, x0, w, args, flush, peak, peak_kind)
+    fwd_d, d_rec = mesh_run(torch, E, Sd, x0, w, args, flush, peak, peak_kind, complete=False)
     if args.only == "fwd":
         clocks.stop()
         if rank == 0:
             print(json.dumps({"only": "fwd", "n": n, "m": m, "C": args.C, "threads": args.threads,
-                              "partitioned_edge_ms": fwd["edge_ms"], "default_edge_ms": fwd_d["edge_ms"],
-                              "partitioned_step_ms": statistics.mean(fwd["ms"]),
-                              "default_step_ms": statistics.mean(fwd_d["ms"]),
-                              "loads": loads, "loads_default": loads_d}))
+                              "partitioned": p_rec, "default": d_rec}))
         return
     iters = max(3, args.steps // 20)
     fb = bench_fwd_bwd(torch, S, x0, w, iters, 3, flush)
     fb_d = bench_fwd_bwd(torch, Sd, x0, w, iters, 3, flush)
-    clk = clocks.stop()
-
-    sweep = {}
-    if args.sweep:
+    tot = max_over_ranks(torch, fwd["total_ms"])
+    value = ws * m * len(fwd["ms"]) / (1e-3 * tot)
+    fb_tot = max_over_ranks(torch, sum(fb["ms"]))
+    fb_value = ws * m * fb["T"] * len(fb["ms"]) / (1e-3 * fb_tot)
+    sweep = None
+    if not args.quick:
+        sweep = {}
         for C in (256, 512, 1024):
-            Sc = E.Schedule.partition(src, dst, n, C)
+            Sc = S if C == args.C else E.Schedule.partition(src, dst, n, C)
             Sc.set_threads(args.threads)
             Sc.set_pipeline(args.stages)
-            r = bench_fwd(torch, E, Sc, x0, w, max(10, args.steps // 4), args.warmup, flush)
-            sweep[str(C)] = dict(edge_updates_per_s=m * len(r["ms"]) / (1e-3 * sum(r["ms"])),
-                                 loads=Sc.cost_host()[0])
+            _, rec = mesh_run(torch, E, Sc, x0, w, args, flush, peak, peak_kind, complete=False)
+            sweep[str(C)] = {k: rec[k] for k in ("edge_updates_per_s", "loads", "vertex_cut", "edge_kernel_ms",
+                                                 "finish_ms", "roofline", "back_to_back")}
+    clk = clocks.stop()
 
     e2e = bench_e2e(torch, S, x0, w)
     e2e["value"] *= ws  # replicas: whole-job aggregate
     e2e["resident_state"]["value"] *= ws
-    tot = max_over_ranks(torch, sum(fwd["ms"]))
-    value = ws * m * len(fwd["ms"]) / (1e-3 * tot)
-    fb_tot = max_over_ranks(torch, sum(fb["ms"]))
-    fb_value = ws * m * fb["T"] * len(fb["ms"]) / (1e-3 * fb_tot)
-
-    # every load beyond a vertex's first block is a foreign record id: sum = vertex cut
-    alg = algorithmic_bytes(S, loads, cut)
-    alg_d = algorithmic_bytes(Sd, loads_d, cut_d)
-    peak, peak_kind = peaks()
-    achieved = alg / (fwd["edge_ms"] * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            tr = json.load(open(tr_path))
-            from paper_1605_02043_gb300 import build as B
-            import hashlib
-            hh = hashlib.sha256()
-            for f in ("flux_tma.cu", "kernels.h", "internal.h"):  # the pipelined kernels' sources
-                hh.update(open(os.path.join(B.CSRC, f), "rb").read())
-            h = hh.hexdigest()[:16]
-            ent = tr.get(f"flux_fwd_C{args.C}_n{n}")
-            if ent and ent.get("kernel_sources_sha") == h:
-                traffic = ent["dram_bytes_per_launch"]
-        except Exception:
-            traffic = None
+    rmat = batch = None
+    if not args.quick:
+        rmat = rmat_record(torch, E, args, ws, flush)
+        batch = batch_record(torch, E, args, ws)
 
     if rank != 0:
         return
@@ -727,28 +834,20 @@ def main():
         "config": mesh_config(args, n, m, ws,
                               f"flushed before every timed step ({flush_bytes >> 20} MiB write then "
                               f"{flush_bytes >> 20} MiB read of scratch buffers, outside the events)"),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "flux_fwd_tma_kernel<5>" if args.stages else "flux_fwd_kernel<5>",
-                     "algorithmic_bytes_per_launch": alg,
-                     "launch_ms": fwd["edge_ms"], "peak_kind": f"{peak_kind} HBM copy"},
+        "roofline": p_rec["roofline"],
         "cpu_baseline": cpu,
         "cpu_all_cores": fair,
         "e2e": e2e,
         "gpu_launches": fwd["launches_timed"],
         "clocks": clk,
-        "partitioned": {"edge_updates_per_s": value, "loads": loads, "vertex_cut": cut,
-                        "edge_kernel_ms": fwd["edge_ms"], "bnd_kernel_ms": fwd["bnd_ms"],
-                        "partition_s": part_s, "alg_bytes": alg,
-                        "alg_GBps_edge_kernel": achieved},
-        "default": {"edge_updates_per_s": ws * m * len(fwd_d["ms"]) / (1e-3 * sum(fwd_d["ms"])),
-                    "loads": loads_d, "vertex_cut": cut_d, "edge_kernel_ms": fwd_d["edge_ms"],
-                    "bnd_kernel_ms": fwd_d["bnd_ms"], "alg_bytes": alg_d,
-                    "alg_GBps_edge_kernel": alg_d / (fwd_d["edge_ms"] * 1e-3) / 1e9},
+        "partitioned": dict(p_rec, partition_s=part_s),
+        "default": d_rec,
         "fwd_bwd": {"partitioned": fb_value,
                     "default": ws * m * fb_d["T"] * len(fb_d["ms"]) / (1e-3 * sum(fb_d["ms"])),
                     "unit": UNIT, "steps": fb["T"], "checkpoint_every": 5, "iterations": len(fb["ms"])},
-        "C_sweep": sweep or None,
+        "C_sweep": sweep,
+        "rmat": rmat,
+        "batch": batch,
     }
     print(json.dumps(line))
 

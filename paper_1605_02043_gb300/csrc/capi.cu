@@ -387,8 +387,9 @@ int flux_step_any(ep_schedule* s, int32_t D, const float* w, const float* x_in, 
                   float* out, float tau, bool finish, cudaStream_t st) {
   ep::dev::FluxArgs a = flux_args(s, kFwd, w, x_in, x_out, out, tau);
   if (s->cache == EP_CACHE_L1) {
-    // the read-only-cache kernel reads x_in in place: finish it first
-    if (int rc = finish_any(s, kFwd, D, x_in, const_cast<float*>(x_in), nullptr, tau, st)) return rc;
+    // the read-only-cache kernel reads x_in in place: finish a pending input first
+    if (s->pending[kFwd])
+      if (int rc = finish_any(s, kFwd, D, x_in, const_cast<float*>(x_in), nullptr, tau, st)) return rc;
     CU(ep::dev::flux_step_ldg(a, D, st));
   } else {
     ep::dev::TmaPlan P;
@@ -412,6 +413,7 @@ int flux_step_any(ep_schedule* s, int32_t D, const float* w, const float* x_in, 
       CU(ep::dev::flux_fwd_tma(a, P, D, st));
     }
   }
+  s->pending[kFwd] = !finish;
   if (finish) return finish_any(s, kFwd, D, x_out, x_out, out, tau, st);
   return EP_OK;
 }
@@ -441,6 +443,7 @@ int flux_adj_any(ep_schedule* s, int32_t D, const float* w, const float* x, floa
     } sc(a.timer, st);
     CU(ep::dev::flux_adj_tma(a, P, D, lam, gw, st));
   }
+  s->pending[kAdj] = !finish;
   if (finish) return finish_any(s, kAdj, D, lam, lam, nullptr, tau, st);
   return EP_OK;
 }
@@ -931,9 +934,7 @@ int step_entry(ep_schedule* s, int32_t D, const float* x_in, float* x_out, const
         CU(cudaMemcpyAsync(x_out + off, x_in + off, bytes, cudaMemcpyDeviceToDevice, st));
     }
   }
-  if (int rc = flux_step_any(s, D, w_lay, x_in, x_out, out_lay, tau, finish, st)) return rc;
-  s->pending[kFwd] = !finish;
-  return EP_OK;
+  return flux_step_any(s, D, w_lay, x_in, x_out, out_lay, tau, finish, st);
 }
 
 }  // namespace
@@ -969,9 +970,7 @@ int ep_adjoint_step(ep_schedule* s, int32_t D, const float* x_lay, const float* 
   if (!grad_w_lay) return fail(EP_EINVAL, "null argument");
   cudaStream_t st = as_stream(stream);
   if (int rc = ensure_bacc(s, D, st)) return rc;
-  if (int rc = flux_adj_any(s, D, w_lay, x_lay, lam, grad_w_lay, tau, true, st)) return rc;
-  s->pending[kAdj] = false;
-  return EP_OK;
+  return flux_adj_any(s, D, w_lay, x_lay, lam, grad_w_lay, tau, true, st);
 }
 
 int ep_adjoint_step_pending(ep_schedule* s, int32_t D, const float* x_lay, const float* w_lay,
@@ -981,9 +980,7 @@ int ep_adjoint_step_pending(ep_schedule* s, int32_t D, const float* x_lay, const
   if (!grad_w_lay) return fail(EP_EINVAL, "null argument");
   cudaStream_t st = as_stream(stream);
   if (int rc = ensure_bacc(s, D, st)) return rc;
-  if (int rc = flux_adj_any(s, D, w_lay, x_lay, lam, grad_w_lay, tau, false, st)) return rc;
-  s->pending[kAdj] = true;
-  return EP_OK;
+  return flux_adj_any(s, D, w_lay, x_lay, lam, grad_w_lay, tau, false, st);
 }
 
 int ep_adjoint_finish(ep_schedule* s, int32_t D, float* lam, float tau, void* stream) {
