@@ -137,7 +137,7 @@ struct ep_schedule {
   int tpb = 192;
   bool bacc_dirty = true;
   // device copy of the schedule
-  DBuf d_desc, d_flist, d_ylist, d_inc, d_ptr, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
+  DBuf d_desc, d_flist, d_ylist, d_ent, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
       d_ev;
   DBuf d_sidx, d_soff, d_sid, d_vrec, d_gslot, d_frec, d_fsid;  // flux layout
   // workspace
@@ -205,8 +205,7 @@ int ensure_device(ep_schedule* s) {
     CU(upload(s->d_desc, h.sdesc));
     CU(upload(s->d_flist, h.xlist));
     CU(upload(s->d_ylist, h.ylist));
-    CU(upload(s->d_inc, h.sinc));
-    CU(upload(s->d_ptr, h.sptr));
+    CU(upload(s->d_ent, h.sent));
     CU(upload(s->d_wmap, h.wmap));
     CU(upload(s->d_xrec, h.xrec_of));
     CU(upload(s->d_yrec, h.yrec_of));
@@ -465,8 +464,7 @@ int spmv_lay(ep_schedule* s, const float* x_lay, const float* w_lay, float* y_la
   a.k = h.k;
   a.xlist = s->d_flist.as<int32_t>();
   a.ylist = s->d_ylist.as<int32_t>();
-  a.inc = s->d_inc.as<uint32_t>();
-  a.ptr = s->d_ptr.as<uint16_t>();
+  a.ent = s->d_ent.as<uint32_t>();
   a.w = w_lay;
   a.x = x_lay;
   a.y = y_lay;
@@ -474,13 +472,19 @@ int spmv_lay(ep_schedule* s, const float* x_lay, const float* w_lay, float* y_la
   a.ny_zero = h.n - h.ny_int;
   a.max_nx = h.max_nx;
   a.max_ny = h.max_ny;
-  a.max_ne = h.max_ne;
+  a.max_nxy = h.max_nxy;
+  a.u = h.spmv_u;
   a.tpb = s->tpb;
   a.readonly = s->cache == EP_CACHE_L1;
   a.timer = s->t();
-  if (!a.readonly) {
-    if (int rc = block_fits(s, ep::dev::spmv_block_smem(a))) return rc;
-  }
+  int dev = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const ep::dev::SpmvPlan P = ep::dev::spmv_plan(a, optin);
+  if (P.wpb == 0)
+    return fail(EP_EINVAL,
+                "a schedule block needs %zu bytes of shared memory (limit %d): use a smaller C",
+                P.smem, optin - 1024);
   CU(ep::dev::spmv(a, st));
   return EP_OK;
 }

@@ -46,24 +46,33 @@ constexpr uint16_t kSlotSrc = 0x8000u;
 constexpr int32_t kSidFirst = INT32_MIN;   // sid_list: first copy of this shared vertex
 constexpr int32_t kSidMask = 0x7fffffff;
 
-// Incidence entry fields (SpMV rows)
-constexpr uint32_t kPosMask = 0x7fffu;
-constexpr int kTaskShift = 15;
+// SpMV entry fields: (row position << 16) | x position
+constexpr int kRowShift = 16;
+constexpr uint32_t kColMask = 0xffffu;
 
 // SpMV kernels (bipartite): x records are read only, y records accumulate.
 // x positions: [0, n_xo) the run x_lo.., then n_xf ids from xlist[fx0..].
 // y positions: [0, n_yi) the single-block rows yi_lo.., [n_yi, n_yi + n_yob)
 // the run yb_lo.. of shared rows first touched here, then n_yf ids from
 // ylist[fy0..]; within each class rows are ordered by descending list length.
-// Row position p has entries ent[i0 + ptr[q0 + p] .. i0 + ptr[q0 + p + 1]):
-// (x position) | (task << 15); task weights are w_lay[w0 .. w0 + ne).
+// The block's ne entries, ranked by row position, go to lane t / u of a warp
+// (u entries per lane, a multiple of 4, the same for every block) and are
+// stored 4 by 4 interleaved over the lanes (spmv_slot), so that one 16-byte
+// load per lane reads 512 consecutive bytes; the task weight of the entry in
+// slot j is w_lay[i0 + j].  Every block's runs hold 32 * u slots (padding:
+// entry 0, weight 0), so block b's start at i0 = 32 * u * b.
 struct SpmvDesc {
-  int32_t w0, ne;
+  int32_t i0, ne, u;
   int32_t x_lo, n_xo, fx0, n_xf;
   int32_t yi_lo, n_yi, yb_lo, n_yob, fy0, n_yf;
-  int32_t i0, q0, pad[2];
+  int32_t pad[3];
 };
 static_assert(sizeof(SpmvDesc) == 64, "SpmvDesc layout");
+// slot (from i0) of the entry ranked t in row order, u entries per lane
+inline int32_t spmv_slot(int32_t t, int32_t u) {
+  const int32_t lane = t / u, j = t % u;
+  return ((j >> 2) * 32 + lane) * 4 + (j & 3);
+}
 
 // Host part of a schedule plus the kernel layout derived from it.
 struct HostSchedule {
@@ -94,16 +103,16 @@ struct HostSchedule {
   int32_t max_nv = 0, max_nslot = 0, max_nsh = 0, max_nsl = 0;
   int64_t w_pad = 0;           // slots of the weight layout
   std::vector<int32_t> wmap;   // weight slot -> task id (-1 for padding)
-  int32_t max_nent = 0;        // SpMV: max row entries per block
 
   // spmv layout (bipartite): x records 0..n-1, y records 0..n-1
   int64_t ny_int = 0, ny_bnd = 0;
   std::vector<int32_t> xrec_of, yrec_of;  // by column / row index
   std::vector<SpmvDesc> sdesc;
   std::vector<int32_t> xlist, ylist;
-  std::vector<uint32_t> sinc;   // SpMV row entries
-  std::vector<uint16_t> sptr;   // SpMV row offsets
+  std::vector<uint32_t> sent;   // SpMV entries (padded runs, see SpmvDesc)
   int32_t max_nx = 0, max_ny = 0;
+  int32_t max_nxy = 0;  // largest x + y positions of a block, each rounded up to 4
+  int32_t spmv_u = 0;   // entries per lane (every block: 32 * spmv_u slots)
 };
 
 // prescreen.cpp: checks made before partitioning (Section 4 workflow).

@@ -184,103 +184,183 @@ __global__ void __launch_bounds__(1024) flux_adj_kernel(const FluxArgs a, float*
 
 // --------------------------------------------------------------------- SpMV
 
-// One CUDA block per schedule block, pull form: x of the block's columns is
-// staged in shared memory; every row position sums w * x over its list.
-// Rows with more than 32 entries (hubs of a power-law matrix) take a whole
-// warp each; the others one thread each.
-__device__ __forceinline__ void spmv_write(const SpmvDesc& d, const int32_t* __restrict__ ylist,
-                                           float* __restrict__ y, int p, float acc) {
-  if (p < d.n_yi) {
-    y[d.yi_lo + p] = acc;
-  } else {
-    const int own = d.n_yi + d.n_yob;
-    const int32_t r = p < own ? d.yb_lo + (p - d.n_yi) : __ldg(ylist + d.fy0 + (p - own));
-    atomicAdd(y + r, acc);
-  }
+// SpMV over the edge partition (Section 5.2), one warp per schedule block.
+// The block's entries are ranked by row position and cut into 32 equal
+// chunks, one per lane, so every lane does the same work whatever the row
+// lengths: a lane walks its chunk in order, summing runs of equal rows in a
+// register.  A run that neither starts nor ends the chunk is a whole row and
+// is stored at once; the first and last runs of the chunks are joined across
+// lanes by a segmented scan over the warp.  Row totals go to a shared array
+// and leave it in row order (plain stores for rows of this block alone,
+// atomics for shared rows).  With the software cache, x of the block's
+// columns is staged in shared memory first; the read-only-cache variant
+// reads x through the read-only data cache at every entry.
+//
+// Per-warp shared region: y totals at [0, ceil4(ny)), staged x after them.
+constexpr int kSpmvBatch = 4;  // 16-byte chunks of entries (and weights) in flight per lane
+constexpr int kSpmvMaxThreads = 256;
+
+__device__ __forceinline__ int spmv_up4(int v) { return (v + 3) & ~3; }
+
+template <bool STAGE>
+__device__ __forceinline__ float spmv_x(const SpmvDesc& d, const int32_t* __restrict__ xlist,
+                                        const float* __restrict__ x, const float* xs, uint32_t col) {
+  if (STAGE) return xs[col];
+  const int c = (int)col;
+  return __ldg(x + (c < d.n_xo ? d.x_lo + c : __ldg(xlist + d.fx0 + (c - d.n_xo))));
 }
 
-__global__ void __launch_bounds__(1024) spmv_kernel(
-    const SpmvDesc* __restrict__ desc, const int32_t* __restrict__ xlist,
-    const int32_t* __restrict__ ylist, const uint32_t* __restrict__ inc,
-    const uint16_t* __restrict__ ptr, const float* __restrict__ w, const float* __restrict__ x,
-    float* __restrict__ y) {
-  extern __shared__ float4 smem4[];
-  const SpmvDesc d = desc[blockIdx.x];
-  const int nx = d.n_xo + d.n_xf, ny = d.n_yi + d.n_yob + d.n_yf;
-  float* xs = reinterpret_cast<float*>(smem4);
-  float* ws = xs + ((nx + 3) & ~3);
-  uint32_t* es = reinterpret_cast<uint32_t*>(ws + ((d.ne + 3) & ~3));
-  uint16_t* ps = reinterpret_cast<uint16_t*>(es + d.ne);
-  // weights, entries and row offsets: four loads in flight per thread
-  for (int i0 = threadIdx.x; i0 < d.ne; i0 += 4 * blockDim.x) {
-    float wv[4];
-    uint32_t ev[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * (int)blockDim.x;
-      wv[u] = i < d.ne ? __ldg(w + d.w0 + i) : 0.f;
-      ev[u] = i < d.ne ? __ldg(inc + d.i0 + i) : 0u;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * (int)blockDim.x;
-      if (i < d.ne) {
-        ws[i] = wv[u];
-        es[i] = ev[u];
-      }
-    }
-  }
-  for (int i0 = threadIdx.x; i0 <= ny; i0 += 4 * blockDim.x) {
-    uint16_t pv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * (int)blockDim.x;
-      pv[u] = i <= ny ? __ldg(ptr + d.q0 + i) : (uint16_t)0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * (int)blockDim.x;
-      if (i <= ny) ps[i] = pv[u];
-    }
-  }
-  // x entries: four (id, value) load chains in flight per thread
-  for (int i0 = threadIdx.x; i0 < nx; i0 += 4 * blockDim.x) {
+// x of the block's columns into xs: four (id, value) load chains in flight
+// per lane
+__device__ __forceinline__ void spmv_stage_x(const SpmvDesc& d, const SpmvArgs& a, float* xs, int lane) {
+  const int nx = d.n_xo + d.n_xf;
+  for (int i0 = lane; i0 < nx; i0 += 4 * 32) {
     int32_t r[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * (int)blockDim.x;
-      r[u] = i >= nx ? -1 : (i < d.n_xo ? d.x_lo + i : __ldg(xlist + d.fx0 + (i - d.n_xo)));
+      const int i = i0 + 32 * u;
+      r[u] = i >= nx ? -1 : (i < d.n_xo ? d.x_lo + i : __ldg(a.xlist + d.fx0 + (i - d.n_xo)));
     }
     float v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = r[u] >= 0 ? __ldg(x + r[u]) : 0.f;
+    for (int u = 0; u < 4; ++u) v[u] = r[u] >= 0 ? __ldg(a.x + r[u]) : 0.f;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (r[u] >= 0) xs[i0 + u * (int)blockDim.x] = v[u];
+      if (r[u] >= 0) xs[i0 + 32 * u] = v[u];
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int p = warp; p < ny; p += nw) {
-    const int k0 = ps[p], k1 = ps[p + 1];
-    if (k1 - k0 <= 32) continue;  // warp-uniform
-    float acc = 0.f;
-    for (int q = k0 + lane; q < k1; q += 32) {
-      const uint32_t e = es[q];
-      acc = fmaf(ws[e >> kTaskShift], xs[e & kPosMask], acc);
+}
+
+struct SpmvRun {
+  int cur = -1, hrow = -1;  // row of the open run; row of the chunk's first run once closed
+  float acc = 0.f, hsum = 0.f;
+  bool whole = true;  // no run closed yet: the chunk is one run so far
+};
+
+__device__ __forceinline__ void spmv_take(SpmvRun& r, float* ys, uint32_t e, float v) {
+  const int row = (int)(e >> kRowShift);
+  if (row != r.cur) {
+    if (r.cur >= 0) {
+      if (r.whole) {
+        r.hrow = r.cur;
+        r.hsum = r.acc;
+        r.whole = false;
+      } else {
+        ys[r.cur] = r.acc;  // a run inside the chunk: the whole row
+      }
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) spmv_write(d, ylist, y, p, acc);
+    r.cur = row;
+    r.acc = v;
+  } else {
+    r.acc += v;
   }
-  for (int p = threadIdx.x; p < ny; p += blockDim.x) {
-    const int k0 = ps[p], k1 = ps[p + 1];
-    if (k1 - k0 > 32 || k1 == k0) continue;
-    float acc = 0.f;
-    for (int q = k0; q < k1; ++q) {
-      const uint32_t e = es[q];
-      acc = fmaf(ws[e >> kTaskShift], xs[e & kPosMask], acc);
+}
+
+// Four entries (one 16-byte chunk) of this lane; j: their rank in the chunk
+template <bool STAGE>
+__device__ __forceinline__ void spmv_chunk(SpmvRun& run, float* ys, const float* xs, const SpmvDesc& d,
+                                           const SpmvArgs& a, uint4 ev, float4 wv, int j, int nj) {
+  const uint32_t e[4] = {ev.x, ev.y, ev.z, ev.w};
+  const float w[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (j + q < nj) spmv_take(run, ys, e[q], w[q] * spmv_x<STAGE>(d, a.xlist, a.x, xs, e[q] & kColMask));
+}
+
+// Joins the chunks' end runs: lane l's first run continues lane l-1's last
+// run when both are the same row, and a lane whose chunk is one run passes
+// the sum on (segmented inclusive scan of the last-run sums over the lanes).
+// Afterwards every row of the block has its total in ys, stored once.
+__device__ __forceinline__ void spmv_join(const SpmvRun& run, float* ys, int lane) {
+  const unsigned full = 0xffffffffu;
+  const int rt = run.cur, rh = run.whole ? run.cur : run.hrow;
+  const int rt_prev = __shfl_up_sync(full, rt, 1);
+  const bool cont = lane > 0 && rh >= 0 && rh == rt_prev;
+  float S = run.acc;
+  int F = !(run.whole && cont);  // a segment starts here
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float Sp = __shfl_up_sync(full, S, o);
+    const int Fp = __shfl_up_sync(full, F, o);
+    if (lane >= o && !F) {
+      S += Sp;
+      F = Fp;
     }
-    spmv_write(d, ylist, y, p, acc);
   }
+  const float S_prev = __shfl_up_sync(full, S, 1);
+  const int cont_next = __shfl_down_sync(full, (int)cont, 1);
+  if (!run.whole) ys[rh] = run.hsum + (cont ? S_prev : 0.f);
+  if (rt >= 0 && !(lane < 31 && cont_next)) ys[rt] = S;
+}
+
+// Row totals out: four rows in flight per lane
+__device__ __forceinline__ void spmv_write_out(const SpmvDesc& d, const SpmvArgs& a, const float* ys,
+                                               int lane) {
+  const int ny = d.n_yi + d.n_yob + d.n_yf, own = d.n_yi + d.n_yob;
+  for (int p0 = lane; p0 < ny; p0 += 4 * 32) {
+    int32_t r[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int p = p0 + 32 * u;
+      r[u] = p >= ny ? -1
+                     : (p < d.n_yi ? d.yi_lo + p
+                                   : (p < own ? d.yb_lo + (p - d.n_yi)
+                                              : __ldg(a.ylist + d.fy0 + (p - own))));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int p = p0 + 32 * u;
+      if (r[u] < 0) continue;
+      if (p < d.n_yi)
+        a.y[r[u]] = ys[p];
+      else
+        atomicAdd(a.y + r[u], ys[p]);
+    }
+  }
+}
+
+// One warp per schedule block (one pass, no pipeline): the lane's entries and
+// weights are loaded straight into registers while x is staged.
+template <bool STAGE>
+__global__ void __launch_bounds__(kSpmvMaxThreads) spmv_kernel(const SpmvArgs a, int wpb, int cap) {
+  extern __shared__ float4 smem4[];
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * wpb + wi;
+  if (b >= a.k) return;  // warp-uniform; the warps of a CUDA block never synchronise
+  const SpmvDesc d = a.desc[b];
+  float* ys = reinterpret_cast<float*>(smem4) + (size_t)wi * cap;
+  float* xs = ys + spmv_up4(d.n_yi + d.n_yob + d.n_yf);
+  const int nj = min(max(d.ne - lane * d.u, 0), d.u);  // this lane's real entries
+  // chunk c of this lane: slots i0 + (32 c + lane) * 4 .. + 3
+  const uint4* ep = reinterpret_cast<const uint4*>(a.ent + d.i0) + lane;
+  const float4* wp = reinterpret_cast<const float4*>(a.w + d.i0) + lane;
+  uint4 ev[kSpmvBatch];
+  float4 wv[kSpmvBatch];
+#pragma unroll
+  for (int c = 0; c < kSpmvBatch; ++c)
+    if (4 * c < nj) {
+      ev[c] = __ldg(ep + 32 * c);
+      wv[c] = __ldg(wp + 32 * c);
+    }
+  if (STAGE) {
+    spmv_stage_x(d, a, xs, lane);
+    __syncwarp();
+  }
+  SpmvRun run;
+  for (int c0 = 0; 4 * c0 < nj; c0 += kSpmvBatch) {
+    if (c0 > 0) {
+#pragma unroll
+      for (int c = 0; c < kSpmvBatch; ++c)
+        if (4 * (c0 + c) < nj) {
+          ev[c] = __ldg(ep + 32 * (c0 + c));
+          wv[c] = __ldg(wp + 32 * (c0 + c));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kSpmvBatch; ++c) spmv_chunk<STAGE>(run, ys, xs, d, a, ev[c], wv[c], 4 * (c0 + c), nj);
+  }
+  spmv_join(run, ys, lane);
+  __syncwarp();
+  spmv_write_out(d, a, ys, lane);
 }
 
 // ------------------------------------------------------------------- layout
@@ -584,73 +664,41 @@ cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, c
   return cudaErrorInvalidValue;
 }
 
-// Read-only-cache SpMV (EP-text of Section 5): the same row-pull form with
-// nothing staged; x, the task weights, entries and offsets are read through
-// the read-only data cache.  y is written as in spmv_kernel.
-__global__ void __launch_bounds__(1024) spmv_ldg_kernel(
-    const SpmvDesc* __restrict__ desc, const int32_t* __restrict__ xlist,
-    const int32_t* __restrict__ ylist, const uint32_t* __restrict__ inc,
-    const uint16_t* __restrict__ ptr, const float* __restrict__ w, const float* __restrict__ x,
-    float* __restrict__ y) {
-  const SpmvDesc d = desc[blockIdx.x];
-  const int ny = d.n_yi + d.n_yob + d.n_yf;
-  const uint32_t* es = inc + d.i0;
-  const uint16_t* ps = ptr + d.q0;
-  const float* ws = w + d.w0;
-  auto xval = [&](uint32_t e) {
-    const int i = (int)(e & kPosMask);
-    return __ldg(x + (i < d.n_xo ? d.x_lo + i : __ldg(xlist + d.fx0 + (i - d.n_xo))));
-  };
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int p = warp; p < ny; p += nw) {
-    const int k0 = __ldg(ps + p), k1 = __ldg(ps + p + 1);
-    if (k1 - k0 <= 32) continue;  // warp-uniform
-    float acc = 0.f;
-    for (int q = k0 + lane; q < k1; q += 32) {
-      const uint32_t e = __ldg(es + q);
-      acc = fmaf(__ldg(ws + (e >> kTaskShift)), xval(e), acc);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) spmv_write(d, ylist, y, p, acc);
-  }
-  for (int p = threadIdx.x; p < ny; p += blockDim.x) {
-    const int k0 = __ldg(ps + p), k1 = __ldg(ps + p + 1);
-    if (k1 - k0 > 32 || k1 == k0) continue;
-    float acc = 0.f;
-    for (int q = k0; q < k1; ++q) {
-      const uint32_t e = __ldg(es + q);
-      acc = fmaf(__ldg(ws + (e >> kTaskShift)), xval(e), acc);
-    }
-    spmv_write(d, ylist, y, p, acc);
-  }
-}
-
 size_t flux_block_smem(const FluxArgs& a, int D, bool adjoint) {
   return (size_t)tma_layout(a, D, adjoint).stage_bytes;
 }
 
-size_t spmv_block_smem(const SpmvArgs& a) {
-  return (size_t)(a.max_nx + 4) * sizeof(float) + (size_t)(a.max_ne + 4) * 8 +
-         (size_t)(a.max_ny + 1) * sizeof(uint16_t) + 16;
+SpmvPlan spmv_plan(const SpmvArgs& a, int smem_optin) {
+  SpmvPlan P = {};
+  int wpb = std::max(1, std::min(kSpmvMaxThreads / 32, a.tpb / 32));
+  P.cap = a.readonly ? (a.max_ny + 3) & ~3 : a.max_nxy;
+  const size_t per_warp = (size_t)P.cap * sizeof(float);
+  while (wpb > 1 && per_warp * wpb > (size_t)48 * 1024) --wpb;  // room for several CUDA blocks per SM
+  P.smem = per_warp * wpb;
+  P.wpb = P.smem + 1024 <= (size_t)smem_optin ? wpb : 0;
+  return P;
 }
 
 cudaError_t spmv(const SpmvArgs& a, cudaStream_t st) {
-  const size_t smem = spmv_block_smem(a);
-  cudaError_t e = allow_smem(spmv_kernel, smem);
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const SpmvPlan P = spmv_plan(a, optin);
+  if (P.wpb == 0) return cudaErrorInvalidValue;
+  e = a.readonly ? allow_smem(spmv_kernel<false>, P.smem) : allow_smem(spmv_kernel<true>, P.smem);
   if (e != cudaSuccess) return e;
   if (a.ny_zero > 0) {
     e = cudaMemsetAsync(a.y + a.ny_int, 0, (size_t)a.ny_zero * sizeof(float), st);
     if (e != cudaSuccess) return e;
   }
-  if (a.k > 0) {
-    Scope sc(a.timer, T_SPMV, st);
-    if (a.readonly)
-      spmv_ldg_kernel<<<(unsigned)a.k, a.tpb, 0, st>>>(a.desc, a.xlist, a.ylist, a.inc, a.ptr, a.w,
-                                                       a.x, a.y);
-    else
-      spmv_kernel<<<(unsigned)a.k, a.tpb, smem, st>>>(a.desc, a.xlist, a.ylist, a.inc, a.ptr, a.w,
-                                                      a.x, a.y);
-  }
+  if (a.k <= 0) return cudaSuccess;
+  Scope sc(a.timer, T_SPMV, st);
+  const unsigned grid = (unsigned)((a.k + P.wpb - 1) / P.wpb);
+  if (a.readonly)
+    spmv_kernel<false><<<grid, 32 * P.wpb, P.smem, st>>>(a, P.wpb, P.cap);
+  else
+    spmv_kernel<true><<<grid, 32 * P.wpb, P.smem, st>>>(a, P.wpb, P.cap);
   return cudaGetLastError();
 }
 

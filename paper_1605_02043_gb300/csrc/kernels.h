@@ -46,15 +46,15 @@ struct SpmvArgs {
   int64_t k;
   const int32_t* xlist;
   const int32_t* ylist;
-  const uint32_t* inc;   // row entries
-  const uint16_t* ptr;   // row offsets
-  const float* w;        // padded weight layout
+  const uint32_t* ent;   // entries, (row position << 16) | x position
+  const float* w;        // weight layout (one weight per entry, same index)
   const float* x;        // x records
   float* y;              // y records; [ny_int, ny_int + ny_zero) zeroed first
   int64_t ny_int, ny_zero;
-  int32_t max_nx, max_ny, max_ne;
-  int tpb;
-  bool readonly = false;  // spmv_ldg_kernel: nothing staged
+  int32_t max_nx, max_ny, max_nxy;
+  int32_t u;              // entries per lane (every block's runs: 32 u slots)
+  int tpb;                // threads per CUDA block (one warp per schedule block)
+  bool readonly = false;  // x read through the read-only cache, not staged
   Timer* timer;
 };
 
@@ -106,7 +106,14 @@ cudaError_t flux_adjoint_step(const FluxArgs& a, int D, float* lam, float* gw, c
 cudaError_t spmv(const SpmvArgs& a, cudaStream_t st);
 // shared memory the one-block kernels stage for the schedule's largest block
 size_t flux_block_smem(const FluxArgs& a, int D, bool adjoint);
-size_t spmv_block_smem(const SpmvArgs& a);
+// SpMV launch shape: warps (schedule blocks) per CUDA block and the shared
+// memory of one CUDA block; 0 warps when one warp's share does not fit
+struct SpmvPlan {
+  int wpb;      // warps per CUDA block (0: does not fit)
+  int cap;      // floats of the per-warp x / y region
+  size_t smem;  // dynamic shared memory per CUDA block
+};
+SpmvPlan spmv_plan(const SpmvArgs& a, int smem_optin);
 // flux layout in: record r of x_lay <- x[.][vrec[r]] (0 where vrec[r] < 0), n data
 // vertices, state planes of n_rec records
 cudaError_t layout_in_rec(const int32_t* vrec, int64_t n, int64_t n_rec, int D, const float* x,

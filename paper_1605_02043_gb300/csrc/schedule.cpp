@@ -391,19 +391,18 @@ std::string spmv_layout(HostSchedule& s) {
     if (s.yrec_of[i] < 0) s.yrec_of[i] = ny++;
   s.xlist.clear();
   s.ylist.clear();
-  s.sinc.clear();
-  s.sptr.clear();
+  s.sent.clear();
   s.wmap.clear();
-  s.max_nx = s.max_ny = 0;
-  s.max_nent = 0;
+  s.max_nx = s.max_ny = s.max_nxy = 0;
   std::vector<int32_t> pos(s.nd, -1), cnt;
-  std::vector<uint32_t> ent;
+  // one entry run of 32 * u slots per block (u from the largest block), so
+  // that block b's run starts at slot 32 * u * b
+  int64_t big = 0;
+  for (int64_t b = 0; b < s.k; ++b) big = std::max(big, s.block_ptr[b + 1] - s.block_ptr[b]);
+  s.spmv_u = (int32_t)(((big + 31) / 32 + 3) / 4 * 4);
   for (int64_t b = 0; b < s.k; ++b) {
     SpmvDesc& d = s.sdesc[b];
     d.ne = (int32_t)(s.block_ptr[b + 1] - s.block_ptr[b]);
-    while (s.wmap.size() % 4) s.wmap.push_back(-1);
-    d.w0 = (int32_t)s.wmap.size();
-    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) s.wmap.push_back(s.edge_perm[i]);
     d.fx0 = (int32_t)s.xlist.size();
     d.fy0 = (int32_t)s.ylist.size();
     int32_t nxf = 0;
@@ -434,10 +433,13 @@ std::string spmv_layout(HostSchedule& s) {
     d.n_yf = nyf;
     for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
     const int32_t nxs = d.n_xo + nxf, nys = d.n_yi + d.n_yob + nyf;
-    if (nxs > (int32_t)kPosMask + 1 || nys > 65535) return "block touches too many vertices";
+    if (nxs > (int32_t)kColMask + 1 || nys > (int32_t)kColMask + 1)
+      return "block touches too many vertices";
     s.max_nx = std::max(s.max_nx, nxs);
     s.max_ny = std::max(s.max_ny, nys);
-    // row lists: (x position) | (task << 15), tasks in schedule order
+    s.max_nxy = std::max(s.max_nxy, ((nxs + 3) & ~3) + ((nys + 3) & ~3));
+    // entries sorted by row position (a counting sort; schedule order within
+    // a row), each lane of the kernel's warp taking u consecutive ones
     cnt.assign(nys + 1, 0);
     for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
       int32_t u, v;
@@ -445,20 +447,21 @@ std::string spmv_layout(HostSchedule& s) {
       ++cnt[pos[u] + 1];
     }
     for (int32_t q = 0; q < nys; ++q) cnt[q + 1] += cnt[q];
-    d.i0 = (int32_t)s.sinc.size();
-    d.q0 = (int32_t)s.sptr.size();
-    for (int32_t q = 0; q <= nys; ++q) s.sptr.push_back((uint16_t)cnt[q]);
-    ent.assign(d.ne, 0);
+    d.u = s.spmv_u;
+    d.i0 = (int32_t)s.sent.size();
+    const size_t run = (size_t)32 * d.u;
+    s.sent.resize(d.i0 + run, 0u);
+    s.wmap.resize(d.i0 + run, -1);
     for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
       int32_t u, v;
       task_ends(s, s.edge_perm[i], u, v);
-      ent[cnt[pos[u]]++] = (uint32_t)pos[v] | ((uint32_t)(i - s.block_ptr[b]) << kTaskShift);
+      const int32_t t = cnt[pos[u]]++;  // rank in row order
+      const int32_t j = d.i0 + spmv_slot(t, d.u);
+      s.sent[j] = ((uint32_t)pos[u] << kRowShift) | (uint32_t)pos[v];
+      s.wmap[j] = s.edge_perm[i];
     }
-    s.sinc.insert(s.sinc.end(), ent.begin(), ent.end());
-    s.max_nent = std::max(s.max_nent, d.ne);
-    if (s.sinc.size() >= (size_t)INT32_MAX) return "schedule too large";
+    if (s.sent.size() >= (size_t)INT32_MAX) return "schedule too large";
   }
-  while (s.wmap.size() % 4) s.wmap.push_back(-1);
   s.w_pad = (int64_t)s.wmap.size();
   return "";
 }

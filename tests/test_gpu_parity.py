@@ -216,8 +216,9 @@ def test_spmv_read_only_cache(C, default_order):
     check_field(y, O.spmv(r, c, x0, w, n), "y")
 
 
-@pytest.mark.parametrize("C,default_order,threads", [(512, False, 192), (512, True, 192), (64, False, 64),
-                                                     (2048, True, 256), (1000, False, 1024)])
+@pytest.mark.parametrize("C,default_order,threads", [
+    (512, False, 192), (512, True, 192), (512, True, 256), (64, False, 64), (2048, True, 256),
+    (2048, False, 128), (1000, False, 1024), (37, False, 32)])
 def test_spmv_rmat(C, default_order, threads):
     scale = 12
     n = 1 << scale
@@ -244,6 +245,7 @@ def test_spmv_rmat(C, default_order, threads):
     y2 = torch.empty(n, device="cuda")
     S.spmv_y_out(yl, y2)
     check_field(y2, ref, "y (layout entry points)")
+    assert S.check_errors() == 0
 
 
 @pytest.mark.parametrize("stages", [0, 3])
