@@ -215,8 +215,14 @@ int ep_run(ep_schedule *s, int32_t kernel, float *x, const float *w, float *out,
 
 /*
  * No counterpart in the paper (a host-buffer convenience of this library).
- * Same as ep_run with HOST pointers (x in/out, w in, out optional): copies
- * inputs to the device, runs, copies results back and synchronises.
+ * Same as ep_run with HOST pointers (x in/out, w in, out optional); returns
+ * after the results are in host memory (synchronises the stream).  When all
+ * of x, w (and out) are pinned through CUDA (cudaHostAlloc, cudaHostRegister,
+ * a pinned torch tensor), the layout kernels read x in vertex order and w in
+ * task order straight over the host link and write the results back the same
+ * way, with no staging copy; any other host memory is staged through device
+ * buffers with cudaMemcpyAsync.  The buffers must not be touched by the host
+ * until the call returns.
  */
 int ep_run_host(ep_schedule *s, int32_t kernel, float *x, const float *w, float *out, int32_t D,
                 int32_t steps, float tau, void *stream);

@@ -143,6 +143,12 @@ struct ep_schedule {
   // workspace
   DBuf ws_x, ws_out, ws_w, ws_bacc, ws_lam, ws_gw, ws_hist, ws_flags, ws_cnt;
   DBuf ws_hx, ws_hw, ws_hout;
+  // vertex-ordered maps for inputs read from host memory (built on first use):
+  // records of every vertex (CSR) and the weight slots of every task (2 each)
+  DBuf d_hptr, d_hrec, d_tslot;
+  bool host_maps = false;
+  const void* zeroed_x = nullptr;  // workspace buffers last cleared whole (their
+  const void* zeroed_w = nullptr;  // padding is never written by the scatter kernels)
   EventTimer timer;
   ep::dev::Timer* t() { return timer.on ? &timer : nullptr; }
   int stages = 3;  // pipelined kernels with this many stages; 0 = one CUDA block per schedule block
@@ -226,6 +232,46 @@ int ensure_device(ep_schedule* s) {
 }
 
 cudaStream_t as_stream(void* p) { return static_cast<cudaStream_t>(p); }
+
+// The device address of p when it is host memory the GPU can read and write
+// directly (pinned through CUDA), else null.
+const void* host_mapped(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // an unregistered pointer is not an error here
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Maps for reading inputs in vertex / task order: every record of a vertex
+// (CSR over the data vertices) and the weight slots of every task.
+int ensure_host_maps(ep_schedule* s) {
+  if (s->host_maps) return EP_OK;
+  const ep::HostSchedule& h = s->h;
+  std::vector<int32_t> tslot(2 * (size_t)h.m, -1);
+  for (size_t j = 0; j < h.wmap.size(); ++j) {
+    const int32_t t = h.wmap[j];
+    if (t < 0) continue;
+    int32_t* sl = &tslot[2 * (size_t)t];
+    (sl[0] < 0 ? sl[0] : sl[1]) = (int32_t)j;
+  }
+  if (!bipartite(s)) {
+    std::vector<int32_t> ptr(h.nd + 1, 0), rec;
+    for (int32_t v : h.vrec)
+      if (v >= 0) ++ptr[v + 1];
+    for (int64_t v = 0; v < h.nd; ++v) ptr[v + 1] += ptr[v];
+    rec.resize(ptr[h.nd]);
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (size_t r = 0; r < h.vrec.size(); ++r)
+      if (h.vrec[r] >= 0) rec[fill[h.vrec[r]]++] = (int32_t)r;
+    CU(upload(s->d_hptr, ptr));
+    CU(upload(s->d_hrec, rec));
+  }
+  CU(upload(s->d_tslot, tslot));
+  s->host_maps = true;
+  return EP_OK;
+}
 
 // weight layout: flux schedules one weight per slot (two per task), SpMV
 // schedules one per task, both padded per block (wmap: slot -> task)
@@ -489,13 +535,33 @@ int spmv_lay(ep_schedule* s, const float* x_lay, const float* w_lay, float* y_la
   return EP_OK;
 }
 
-int run_spmv(ep_schedule* s, const float* x, const float* w, float* y, cudaStream_t st) {
+// Workspace w in schedule layout from the caller's w.  from_host: w is read
+// in task order (it lives in host memory and crosses the host link once,
+// coalesced); the padding slots, never written then, are cleared with the
+// buffer.
+int weights_to_ws(ep_schedule* s, const float* w, bool from_host, cudaStream_t st) {
+  CU(s->ws_w.ensure((size_t)wlen_of(s) * sizeof(float)));
+  if (!from_host) {
+    CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
+    s->zeroed_w = nullptr;
+    return EP_OK;
+  }
+  if (int rc = ensure_host_maps(s)) return rc;
+  if (s->zeroed_w != s->ws_w.p) {
+    CU(cudaMemsetAsync(s->ws_w.p, 0, s->ws_w.bytes, st));
+    s->zeroed_w = s->ws_w.p;
+  }
+  CU(ep::dev::weights_scatter(s->d_tslot.as<int32_t>(), s->h.m, w, s->ws_w.as<float>(), st, s->t()));
+  return EP_OK;
+}
+
+int run_spmv(ep_schedule* s, const float* x, const float* w, float* y, cudaStream_t st,
+             bool from_host = false) {
   const ep::HostSchedule& h = s->h;
   CU(s->ws_x.ensure((size_t)h.n * sizeof(float)));
   CU(s->ws_out.ensure((size_t)h.n * sizeof(float)));
-  CU(s->ws_w.ensure((size_t)wlen_of(s) * sizeof(float)));
   CU(ep::dev::layout_in(s->d_xrec.as<int32_t>(), h.n, h.n, 1, x, s->ws_x.as<float>(), st, s->t()));
-  CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
+  if (int rc = weights_to_ws(s, w, from_host, st)) return rc;
   if (int rc = spmv_lay(s, s->ws_x.as<float>(), s->ws_w.as<float>(), s->ws_out.as<float>(), st))
     return rc;
   CU(ep::dev::layout_out(s->d_yrec.as<int32_t>(), h.n, h.n, 1, s->ws_out.as<float>(), y, st, s->t()));
@@ -997,6 +1063,11 @@ int ep_adjoint_finish(ep_schedule* s, int32_t D, float* lam, float tau, void* st
   return EP_OK;
 }
 
+namespace {
+int run_flux(ep_schedule* s, int32_t D, int32_t steps, float tau, float* x, const float* w, float* out,
+             bool from_host, cudaStream_t st);
+}  // namespace
+
 int ep_run(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out, int32_t D,
            int32_t steps, float tau, void* stream) {
   g_error.clear();
@@ -1014,18 +1085,38 @@ int ep_run(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out,
   if (int rc = check_flux(s, D)) return rc;
   if (steps < 1) return fail(EP_EINVAL, "steps must be >= 1");
   if (int rc = ensure_device(s)) return rc;
+  return run_flux(s, D, steps, tau, x, w, out, false, st);
+}
+
+namespace {
+
+// ep_run's flux part: x, w and out in the caller's layout, device addresses.
+// from_host: x and w are read in vertex / task order (host memory the GPU
+// reads over the host link).
+int run_flux(ep_schedule* s, int32_t D, int32_t steps, float tau, float* x, const float* w, float* out,
+             bool from_host, cudaStream_t st) {
   const ep::HostSchedule& h = s->h;
   const int32_t R = ep::record_floats(D);
   const size_t lay = (size_t)h.n_rec * R * sizeof(float);
   CU(s->ws_x.ensure(lay));
-  CU(s->ws_w.ensure((size_t)wlen_of(s) * sizeof(float)));
   if (out) {
     CU(s->ws_out.ensure(lay));
   }
   fresh_state(s);
   if (int rc = ensure_bacc(s, D, st)) return rc;
-  CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, x, s->ws_x.as<float>(), st, s->t()));
-  CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
+  if (from_host) {
+    if (int rc = ensure_host_maps(s)) return rc;
+    if (s->zeroed_x != s->ws_x.p) {  // records of no vertex stay zero
+      CU(cudaMemsetAsync(s->ws_x.p, 0, s->ws_x.bytes, st));
+      s->zeroed_x = s->ws_x.p;
+    }
+    CU(ep::dev::layout_in_csr(s->d_hptr.as<int32_t>(), s->d_hrec.as<int32_t>(), h.nd, h.n_rec, D, x,
+                              s->ws_x.as<float>(), st, s->t()));
+  } else {
+    CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, x, s->ws_x.as<float>(), st, s->t()));
+    s->zeroed_x = nullptr;
+  }
+  if (int rc = weights_to_ws(s, w, from_host, st)) return rc;
   if (out) CU(cudaMemsetAsync(s->ws_out.p, 0, lay, st));
   // the shared copies stay pending between steps; the last step finishes them
   for (int32_t t = 0; t < steps; ++t) {
@@ -1040,6 +1131,8 @@ int ep_run(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out,
   return EP_OK;
 }
 
+}  // namespace
+
 int ep_run_host(ep_schedule* s, int32_t kernel, float* x, const float* w, float* out, int32_t D,
                 int32_t steps, float tau, void* stream) {
   g_error.clear();
@@ -1048,6 +1141,30 @@ int ep_run_host(ep_schedule* s, int32_t kernel, float* x, const float* w, float*
   if (int rc = ensure_device(s)) return rc;
   cudaStream_t st = as_stream(stream);
   const ep::HostSchedule& h = s->h;
+  // pinned host buffers: the layout kernels read x and w and write the
+  // results over the host link themselves, with no staging copy in between
+  float* dx = const_cast<float*>(static_cast<const float*>(host_mapped(x)));
+  const float* dw = static_cast<const float*>(host_mapped(w));
+  float* dout = out ? const_cast<float*>(static_cast<const float*>(host_mapped(out))) : nullptr;
+  if (dx && dw && (!out || dout)) {
+    int rc;
+    if (kernel == EP_KERNEL_SPMV) {
+      if (!bipartite(s)) return fail(EP_EINVAL, "SpMV needs a bipartite schedule");
+      if (D != 1 || steps != 1) return fail(EP_EINVAL, "SpMV takes D = 1 and steps = 1");
+      if (!out) return fail(EP_EINVAL, "SpMV needs an output vector");
+      rc = run_spmv(s, dx, dw, dout, st, true);
+    } else if (kernel == EP_KERNEL_FLUX) {
+      if ((rc = check_flux(s, D))) return rc;
+      if (steps < 1) return fail(EP_EINVAL, "steps must be >= 1");
+      rc = run_flux(s, D, steps, tau, dx, dw, dout, true, st);
+    } else {
+      return fail(EP_EINVAL, "unknown kernel %d", kernel);
+    }
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(st));
+    return EP_OK;
+  }
+  // other host memory: staged through device buffers by the copy engines
   const size_t xb = (size_t)(kernel == EP_KERNEL_SPMV ? h.n : h.n * D) * sizeof(float);
   CU(s->ws_hx.ensure(xb));
   CU(s->ws_hw.ensure((size_t)h.m * sizeof(float)));

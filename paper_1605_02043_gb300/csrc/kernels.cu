@@ -394,6 +394,33 @@ __global__ void layout_in_rec_kernel(const int32_t* __restrict__ vrec, int64_t n
   }
 }
 
+// x read in vertex order (coalesced, for x in host memory the GPU reads over
+// the host link), every record of vertex v written: recs[ptr[v] .. ptr[v + 1])
+template <int D>
+__global__ void layout_in_csr_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ recs,
+                                     int64_t n, int64_t n_rec, const float* __restrict__ x,
+                                     float* __restrict__ x_lay) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    float t[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) t[c] = x[(size_t)c * n + v];
+    for (int32_t i = __ldg(ptr + v), e = __ldg(ptr + v + 1); i < e; ++i) rec_store<D>(x_lay, n_rec, __ldg(recs + i), t);
+  }
+}
+
+// w read in task order, written to the task's slots (two, -1 for none)
+__global__ void weights_scatter_kernel(const int2* __restrict__ slots, int64_t m, const float* __restrict__ w,
+                                       float* __restrict__ w_lay) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const float v = w[t];
+    const int2 sl = __ldg(slots + t);
+    if (sl.x >= 0) w_lay[sl.x] = v;
+    if (sl.y >= 0) w_lay[sl.y] = v;
+  }
+}
+
 template <int D>
 __global__ void layout_out_kernel(const int32_t* __restrict__ rec_of, int64_t n, int64_t n_rec,
                                   const float* __restrict__ x_lay, float* __restrict__ x) {
@@ -709,6 +736,23 @@ cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, co
 #define EP_LIN(DD) layout_in_kernel<DD><<<g, 256, 0, st>>>(rec_of, n, n_rec, x, x_lay)
   EP_DISPATCH_D(D, EP_LIN)
 #undef EP_LIN
+  return cudaGetLastError();
+}
+
+cudaError_t layout_in_csr(const int32_t* ptr, const int32_t* recs, int64_t n, int64_t n_rec, int D,
+                          const float* x, float* x_lay, cudaStream_t st, Timer* t) {
+  Scope sc(t, T_LAYOUT, st);
+  const int g = grid_for(n, 256);
+#define EP_LIN(DD) layout_in_csr_kernel<DD><<<g, 256, 0, st>>>(ptr, recs, n, n_rec, x, x_lay)
+  EP_DISPATCH_D(D, EP_LIN)
+#undef EP_LIN
+  return cudaGetLastError();
+}
+
+cudaError_t weights_scatter(const int32_t* slots, int64_t m, const float* w, float* w_lay, cudaStream_t st,
+                            Timer* t) {
+  Scope sc(t, T_LAYOUT, st);
+  weights_scatter_kernel<<<grid_for(m, 256), 256, 0, st>>>(reinterpret_cast<const int2*>(slots), m, w, w_lay);
   return cudaGetLastError();
 }
 

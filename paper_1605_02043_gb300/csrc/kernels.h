@@ -123,6 +123,14 @@ cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, co
                       float* x_lay, cudaStream_t st, Timer* t);
 cudaError_t layout_out(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x_lay,
                        float* x, cudaStream_t st, Timer* t);
+// vertex-ordered forms, for inputs the GPU reads from host memory: x plane by
+// plane in vertex order into every record of each vertex (CSR ptr/recs), and
+// w in task order into the task's two slots (slots[2 t], slots[2 t + 1], -1
+// for none)
+cudaError_t layout_in_csr(const int32_t* ptr, const int32_t* recs, int64_t n, int64_t n_rec, int D,
+                          const float* x, float* x_lay, cudaStream_t st, Timer* t);
+cudaError_t weights_scatter(const int32_t* slots, int64_t m, const float* w, float* w_lay, cudaStream_t st,
+                            Timer* t);
 cudaError_t gather(const int32_t* perm, int64_t m, const float* w, float* w_lay, cudaStream_t st,
                    Timer* t);
 cudaError_t scatter_add(const int32_t* perm, int64_t m, const float* w_lay, float* w, cudaStream_t st,

@@ -277,6 +277,35 @@ def test_run_host_matches_device(small_mesh):
     xT, fT = O.flux_steps(src, dst, x0, w, 4, 1e-3)
     check_state(xh, xT, x0, 4, "x")
     check_field(oh, fT, "out")
+    # pageable host memory takes the staged path; a device run in between
+    # rewrites the workspace through the gather kernels
+    xp, wp = np.array(x0, np.float32), np.array(w, np.float32)
+    op = np.zeros_like(xp)
+    S.run_host(xp, wp, op, steps=4, tau=1e-3, D=5)
+    check_state(xp, xT, x0, 4, "x (pageable)")
+    check_field(op, fT, "out (pageable)")
+    xd = cuda(x0)
+    S.run(xd, cuda(w), None, steps=4, tau=1e-3)
+    check_state(xd, xT, x0, 4, "x (device)")
+    xh.copy_(torch.from_numpy(x0))
+    S.run_host(xh, wh, None, steps=4, tau=1e-3, D=5)
+    check_state(xh, xT, x0, 4, "x (pinned again)")
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_run_host_spmv(pinned):
+    n = 1 << 12
+    r, c = W.rmat(scale=12, m_draws=1 << 16, seed=2)
+    x0, w = W.spmv_inputs(n, r.size, 3)
+    S = E.Schedule.partition(r, c, n, 512, bipartite=True)
+    ref = O.spmv(r, c, x0, w, n)
+    for _ in range(2):
+        xh, wh = torch.from_numpy(np.array(x0, np.float32)), torch.from_numpy(np.array(w, np.float32))
+        yh = torch.full((n,), 7.0)
+        if pinned:
+            xh, wh, yh = xh.pin_memory(), wh.pin_memory(), yh.pin_memory()
+        S.run_host(xh, wh, yh, steps=1, kernel=E.SPMV, D=1)
+        check_field(yh, ref, "y")
 
 
 def test_batch_schedule(small_mesh):
