@@ -345,7 +345,8 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
   P.fits = (int64_t)L.stages * L.stage_bytes <= optin;
   if (!P.fits) return EP_OK;  // the launch falls back to one CUDA block per schedule block
   P.smem = (size_t)L.stages * L.stage_bytes;
-  P.threads = 96 + std::min(s->tpb, 928);  // producer warp, two fix-up warps, consumer warps
+  // producer warp, fix-up warps, consumer warps
+  P.threads = 32 * (1 + ep::dev::kFixupWarps) + std::min(s->tpb, 1024 - 32 * (1 + ep::dev::kFixupWarps));
   const void* kern = ep::dev::flux_tma_kernel_ptr(D, adjoint);
   // the limit is a per-kernel attribute shared by every schedule: open it to
   // the device maximum (the launch still asks for P.smem)

@@ -35,7 +35,6 @@ namespace ep {
 namespace dev {
 namespace {
 
-constexpr int kFixupWarps = 2;
 constexpr int kErrTimeoutFull = 1;
 constexpr int kErrTimeoutEmpty = 2;
 
@@ -107,11 +106,11 @@ __device__ __forceinline__ void produce(const FluxDesc& d, const FluxArgs& a, co
 //   warps 1..kFixupWarps: fix-up, bring the staged copies of shared vertices
 //           up to date from the previous step's accumulator (flux_common.cuh)
 //           while the consumers work on earlier stages, then mark the stage
-//           "ready".  Fix-up warp f owns the stages s with s % kFixupWarps ==
-//           f and takes their fills in order: a parity wait only tells the
-//           current phase from the one before it, so every fill of a stage
-//           must be awaited by one thread in order (two warps keep two
-//           stages' gathers in flight);
+//           "ready".  With F = min(kFixupWarps, stages) of them at work,
+//           fix-up warp f owns the stages s with s % F == f and takes their
+//           fills in order: a parity wait only tells the current phase from
+//           the one before it, so every fill of a stage must be awaited by
+//           one thread in order (F warps keep F stages' gathers in flight);
 //   the other warps: consumers, consume(S, d, slice, lane, acc) computes and writes
 //           back one slice, adding the partial sums of shared vertices into
 //           this step's accumulator; the last consumer warp done with a stage
@@ -176,9 +175,10 @@ __device__ __forceinline__ void pipeline(const FluxArgs& a, const float* lam_in,
   } else if (warp <= kFixupWarps) {
     const float* prev = acc_buffer<D>(a, q + 2);
     float* next = acc_buffer<D>(a, q + 1);
-    for (int j = 0;; ++j) {
+    const int nfix = min(kFixupWarps, L.stages);  // a warp past nfix owns no stage
+    for (int j = 0; warp - 1 < nfix; ++j) {
       const int s = j % L.stages;
-      if (s % kFixupWarps != warp - 1) continue;
+      if (s % nfix != warp - 1) continue;
       const uint32_t par = (uint32_t)(j / L.stages) & 1u;
       const bool ok = mbar_wait(&full[s], par);
       if (!__all_sync(0xffffffffu, ok)) {

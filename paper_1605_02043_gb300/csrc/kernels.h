@@ -73,6 +73,9 @@ struct CostArgs {
 // Persistent pipelined kernels (flux_tma.cu): per-stage shared-memory layout
 // (byte offsets, all multiples of 16) and launch plan.
 constexpr int kMaxStages = 8;
+// fix-up warps of the pipelined flux kernels (warps 1..kFixupWarps; one
+// producer warp and the consumer warps besides)
+constexpr int kFixupWarps = 2;
 struct TmaLayout {
   int npos;  // positions per state plane (multiple of 4)
   int off_lam, off_sidx, off_w, off_sid, off_soff, off_desc;

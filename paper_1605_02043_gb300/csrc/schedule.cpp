@@ -115,6 +115,75 @@ void class_order(const HostSchedule& s, int64_t b, const std::vector<int32_t>& d
   std::stable_sort(out.begin(), out.end(), [&](int32_t a, int32_t c) { return deg[a] > deg[c]; });
 }
 
+struct SlotEntry {
+  int32_t o;  // the other position
+  int32_t e;  // task
+  bool src;   // source side of the task (owns its weight-gradient element)
+};
+
+// Places the entries of slice j (positions 32 j + l, l < 32) in its columns.
+// Column by column, each lane takes one of its remaining entries so that the
+// 32 lanes read their other positions from different shared-memory banks as
+// far as the lists allow: different (o mod 8) within each group of 8 lanes
+// (a 16-byte load is served 8 lanes at a time, 4 banks each) and different
+// (o mod 32) over the slice (4-byte loads).  A lane with fewer entries than
+// columns leaves slots unused; an unused slot has weight 0, so its term is
+// exactly zero whatever position it names, and it takes a free bank too.
+void place_slice(HostSchedule& s, const FluxDesc& d, int32_t j, const std::vector<int32_t>& ent_ptr,
+                 std::vector<SlotEntry>& ents) {
+  const int32_t c0 = s.soff[d.q0 + j], K = s.soff[d.q0 + j + 1] - c0;
+  int32_t lo[32], hi[32];
+  for (int l = 0; l < 32; ++l) {
+    const int32_t p = 32 * j + l;
+    lo[l] = p < d.nv ? ent_ptr[p] : 0;
+    hi[l] = p < d.nv ? ent_ptr[p + 1] : 0;
+  }
+  const int32_t npad = std::min(d.nv, 32);  // unused slots name one of the first 32 positions
+  for (int32_t c = 0; c < K; ++c) {
+    uint32_t used32 = 0;
+    uint32_t used8[4] = {0, 0, 0, 0};
+    auto score = [&](int l, int32_t o) {
+      return 2 * (int)((used8[l >> 3] >> (o & 7)) & 1u) + (int)((used32 >> (o & 31)) & 1u);
+    };
+    // lanes that must place an entry in every remaining column go first
+    uint32_t forced_mask = 0;
+    for (int l = 0; l < 32; ++l)
+      if (hi[l] - lo[l] == K - c) forced_mask |= 1u << l;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int l = 0; l < 32; ++l) {
+        const int32_t rem = hi[l] - lo[l];
+        const bool forced = (forced_mask >> l) & 1u;
+        if ((pass == 0) != forced) continue;
+        int32_t best = -1, bs = 4;
+        for (int32_t i = lo[l]; i < hi[l] && bs > 0; ++i) {
+          const int sc = score(l, ents[i].o);
+          if (sc < bs) best = i, bs = sc;
+        }
+        int32_t pad = 0, ps = 4;
+        if (!forced)
+          for (int32_t o = 0; o < npad && ps > 0; ++o) {
+            const int sc = score(l, o);
+            if (sc < ps) pad = o, ps = sc;
+          }
+        const int64_t slot = (int64_t)d.s0 + 32 * ((int64_t)c0 + c) + l;
+        int32_t o;
+        if (rem > 0 && (forced || bs <= ps)) {
+          std::swap(ents[lo[l]], ents[best]);
+          const SlotEntry& t = ents[lo[l]++];
+          o = t.o;
+          s.sidx[slot] = (uint16_t)((uint32_t)t.o | (t.src ? kSlotSrc : 0u));
+          s.wmap[slot] = t.e;
+          if (t.src) s.gslot[t.e] = (int32_t)slot;
+        } else {
+          o = pad;
+          s.sidx[slot] = (uint16_t)pad;  // weight slot stays -1: weight 0
+        }
+        used8[l >> 3] |= 1u << (o & 7);
+        used32 |= 1u << (o & 31);
+      }
+  }
+}
+
 std::string flux_layout_blocks(HostSchedule& s) {
   std::vector<int32_t> p, owner;
   usage(s, p, owner);
@@ -140,7 +209,8 @@ std::string flux_layout_blocks(HostSchedule& s) {
   s.gslot.assign(s.m, -1);
   s.max_nv = s.max_nslot = s.max_nsh = s.max_nsl = 0;
   std::vector<std::vector<int32_t>> copies(n_sh);
-  std::vector<int32_t> deg(s.nd, 0), ord, pos(s.nd, -1), cls, col;
+  std::vector<int32_t> deg(s.nd, 0), ord, pos(s.nd, -1), cls, col, ent_ptr;
+  std::vector<SlotEntry> ents;
   int64_t next = 0;  // next free record
   for (int64_t b = 0; b < s.k; ++b) {
     FluxDesc& d = s.fdesc[b];
@@ -186,39 +256,29 @@ std::string flux_layout_blocks(HostSchedule& s) {
     pad_to(s.soff, 8, (uint16_t)0);
     d.s0 = (int32_t)s.sidx.size();  // a multiple of 32
     d.nslot = 32 * cols;
-    // unused slots (weight 0) point at the lane's own position, or at position
-    // 0 for lanes past the last position: their term is exactly zero, so the
-    // kernels need no test per slot
     s.sidx.resize(s.sidx.size() + d.nslot, 0);
     s.wmap.resize(s.sidx.size(), -1);
-    for (int32_t j = 0; j < d.nsl; ++j)
-      for (int32_t c = s.soff[d.q0 + j]; c < s.soff[d.q0 + j + 1]; ++c)
-        for (int32_t l = 0; l < 32 && 32 * j + l < d.nv; ++l)
-          s.sidx[d.s0 + 32 * (int64_t)c + l] = (uint16_t)(32 * j + l);
-    // fill: every task at both endpoints in task order (a self loop once);
-    // col[q] counts the entries placed at position q so far
-    col.assign(d.nv, 0);
-    auto slot_of = [&](int32_t q) {
-      const int32_t j = q >> 5;
-      return (int64_t)d.s0 + 32 * ((int64_t)s.soff[d.q0 + j] + col[q]) + (q & 31);
-    };
+    // the entries of every position: each task at both endpoints (a self
+    // loop once), the source side flagged
+    ent_ptr.assign(d.nv + 1, 0);
+    for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
+      int32_t u, v;
+      task_ends(s, s.edge_perm[i], u, v);
+      ++ent_ptr[pos[u] + 1];
+      if (v != u) ++ent_ptr[pos[v] + 1];
+    }
+    for (int32_t q = 0; q < d.nv; ++q) ent_ptr[q + 1] += ent_ptr[q];
+    ents.resize(ent_ptr[d.nv]);
+    col.assign(ent_ptr.begin(), ent_ptr.end() - 1);
     for (int64_t i = s.block_ptr[b]; i < s.block_ptr[b + 1]; ++i) {
       const int32_t e = s.edge_perm[i];
       int32_t u, v;
       task_ends(s, e, u, v);
       const int32_t pu = pos[u], pv = pos[v];
-      const int64_t su = slot_of(pu);
-      ++col[pu];
-      s.sidx[su] = (uint16_t)((uint32_t)pv | kSlotSrc);
-      s.wmap[su] = e;
-      s.gslot[e] = (int32_t)su;
-      if (v != u) {
-        const int64_t sv = slot_of(pv);
-        ++col[pv];
-        s.sidx[sv] = (uint16_t)pu;
-        s.wmap[sv] = e;
-      }
+      ents[col[pu]++] = SlotEntry{pv, e, true};
+      if (v != u) ents[col[pv]++] = SlotEntry{pu, e, false};
     }
+    for (int32_t j = 0; j < d.nsl; ++j) place_slice(s, d, j, ent_ptr, ents);
     for (int64_t i = s.vert_ptr[b]; i < s.vert_ptr[b + 1]; ++i) deg[s.vert_list[i]] = 0;
     s.max_nv = std::max(s.max_nv, d.nv);
     s.max_nslot = std::max(s.max_nslot, d.nslot);
