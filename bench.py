@@ -18,11 +18,15 @@ Reported (one JSON line on rank 0):
   back_to_back   steps without L2 flushes between them (state and tasks stay in L2)
   fwd_bwd        10 steps forward + backward (checkpoint every 5, recompute
                  included) through the autograd function, edge updates/s
+  adjoint        the adjoint edge kernel alone: time per launch and its roofline
   roofline       the forward edge kernel: algorithmic bytes per launch (the cost
-                 model of Eq. 1, 4*D bytes per vertex load) / its mean duration
+                 model of Eq. 1, 4*D bytes per vertex load) / its mean duration;
+                 traffic = ncu DRAM bytes per launch from profiles/traffic.json
+                 while the kernel sources hash to the recorded value
+  e2e            ep_run_host with one step per call: host x, w (pinned) read by
+                 the layout kernels over the host link and x written back every
+                 step; resident_state = 100 steps per call
   C_sweep        C in {256, 512, 1024}: value and roofline of each
-  e2e            ep_run_host with one step per call: host x, w (pinned) copied in
-                 and x read back every step; resident_state = 100 steps per call
   cpu_baseline   the FP64 oracle on the host, bounded sample of steps
   rmat           R-MAT scale-20 SpMV sub-record (partitioned vs default order)
   batch          512 uneven meshes sub-record (100 steps fwd+bwd in a CUDA graph)
@@ -32,6 +36,7 @@ from __future__ import annotations
 
 import argparse
 import csv
+import hashlib
 import io
 import json
 import os
@@ -66,8 +71,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--quick", action="store_true",
                     help="mesh line only: no C sweep, R-MAT or batch sub-records")
-    ap.add_argument("--only", default="", choices=["", "fwd"],
-                    help="fwd: time only the forward loops (for profiler runs)")
+    ap.add_argument("--only", default="", choices=["", "fwd", "adj"],
+                    help="fwd / adj: time only the forward loops / the adjoint steps (profiler runs)")
     ap.add_argument("--workload", default="mesh", choices=["mesh", "rmat", "batch"],
                     help="mesh: 1M-node kNN mesh flux steps (with the sub-records); rmat: R-MAT "
                          "scale-20 SpMV alone; batch: 512 uneven meshes alone")
@@ -235,6 +240,33 @@ def adjoint_bytes(S, loads, foreign):
     return 12 * S.m + 32 * S.k + 4 * foreign + 3 * 4 * D * loads
 
 
+ROOT = os.path.dirname(os.path.abspath(__file__))
+
+
+def kernel_sources_sha():
+    """Hash of the library sources the kernels are built from."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1605_02043_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic(key):
+    """ncu DRAM bytes (read + write) per launch recorded in profiles/traffic.json
+    for this kernel and workload, if recorded from the current sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh).get(key)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_sources_sha") != kernel_sources_sha():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def roofline(alg_bytes, launch_ms, kernel, peak, peak_kind, traffic=None):
     achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -274,6 +306,38 @@ def bench_fwd(torch, S, x0, w, steps, warmup, flush, complete=True, b2b_steps=50
     res["b2b_ms_per_step"] = time_once(torch, b2b) / b2b_steps
     S.check_errors()
     return res
+
+
+def bench_adj(torch, S, x0, w, steps, warmup, flush):
+    """Adjoint steps at the state x0 (one edge-kernel launch each, the
+    cotangent's shared copies pending between them, L2 flushed before each,
+    events around each): mean ms per launch."""
+    import workloads as W
+
+    xl = torch.empty(S.layout_floats(D), device="cuda")
+    wl = torch.empty(S.weights_floats(), device="cuda")
+    lam = torch.empty_like(xl)
+    gw = torch.zeros_like(wl)
+    S.layout_in(torch.from_numpy(x0).cuda(), xl)
+    S.weights_in(torch.from_numpy(w).cuda(), wl)
+    S.layout_in(torch.from_numpy(W.loss_weights(S.n, D, 1).astype(np.float32)).cuda(), lam)
+    step = lambda: S.adjoint_step(D, xl, wl, lam, gw, TAU, pending=True)  # noqa: E731
+    for _ in range(warmup):
+        step()
+    ms = timed_loop(torch, step, steps, 0, flush)
+    S.adjoint_finish(D, lam, TAU)
+    S.check_errors()
+    return statistics.mean(ms)
+
+
+def adjoint_record(torch, S, x0, w, args, flush, peak, peak_kind):
+    loads, cut = S.cost()
+    ms = bench_adj(torch, S, x0, w, max(20, args.steps // 2), args.warmup, flush)
+    alg = adjoint_bytes(S, loads, cut)
+    return {"edge_kernel_ms": ms, "edge_updates_per_s": S.m / (1e-3 * ms), "alg_bytes": alg,
+            "roofline": roofline(alg, ms, "flux_adj_tma_kernel<5>" if args.stages else "flux_adj_kernel<5>",
+                                 peak, peak_kind, traffic(f"flux_adj_{S.origin}_C{S.C}_n{S.n}")),
+            "note": "adjoint steps with the cotangent's shared copies pending, L2 flushed before each"}
 
 
 def bench_fwd_bwd(torch, S, x0, w, iters, warmup, flush, T=10, every=5):
@@ -732,7 +796,8 @@ def mesh_run(torch, E, S, x0, w, args, flush, peak, peak_kind, complete=True):
     rec = {"edge_updates_per_s": m * len(r["ms"]) / (1e-3 * r["total_ms"]), "loads": loads, "vertex_cut": cut,
            "edge_kernel_ms": r["edge_ms"], "finish_ms": r["finish_ms"], "alg_bytes": alg,
            "roofline": roofline(alg, r["edge_ms"], "flux_fwd_tma_kernel<5>" if args.stages else
-                                "flux_fwd_kernel<5>", peak, peak_kind),
+                                "flux_fwd_kernel<5>", peak, peak_kind,
+                                traffic(f"flux_fwd_{S.origin}_C{S.C}_n{S.n}")),
            "back_to_back": {"ms_per_step": r["b2b_ms_per_step"],
                             "edge_updates_per_s": m / (1e-3 * r["b2b_ms_per_step"]),
                             "note": "50 pending steps and their finish without L2 flushes"}}
@@ -788,6 +853,13 @@ def main():
             print(json.dumps({"study": "cache", "n": n, "m": m, "D": D, "threads": args.threads,
                               "rows": rows, "clocks": clk}))
         return
+    if args.only == "adj":
+        rec = adjoint_record(torch, S, x0, w, args, flush, peak, peak_kind)
+        clocks.stop()
+        if rank == 0:
+            print(json.dumps({"only": "adj", "n": n, "m": m, "C": args.C, "threads": args.threads,
+                              "partitioned": rec}))
+        return
     fwd, p_rec = mesh_run(torch, E, S, x0, w, args, flush, peak, peak_kind)
     fwd_d, d_rec = mesh_run(torch, E, Sd, x0, w, args, flush, peak, peak_kind, complete=False)
     if args.only == "fwd":
@@ -796,6 +868,7 @@ def main():
             print(json.dumps({"only": "fwd", "n": n, "m": m, "C": args.C, "threads": args.threads,
                               "partitioned": p_rec, "default": d_rec}))
         return
+    adj = adjoint_record(torch, S, x0, w, args, flush, peak, peak_kind)
     iters = max(3, args.steps // 20)
     fb = bench_fwd_bwd(torch, S, x0, w, iters, 3, flush)
     fb_d = bench_fwd_bwd(torch, Sd, x0, w, iters, 3, flush)
@@ -845,6 +918,7 @@ def main():
         "fwd_bwd": {"partitioned": fb_value,
                     "default": ws * m * fb_d["T"] * len(fb_d["ms"]) / (1e-3 * sum(fb_d["ms"])),
                     "unit": UNIT, "steps": fb["T"], "checkpoint_every": 5, "iterations": len(fb["ms"])},
+        "adjoint": adj,
         "C_sweep": sweep,
         "rmat": rmat,
         "batch": batch,
