@@ -341,7 +341,7 @@ __device__ __forceinline__ void fixup_copies(const FluxDesc& d, float* xs, int n
 // x_out[r] = x_in[r] + tau * prev[h] (every copy holds the same value, so every
 // copy ends with the same new value), out[r] = prev[h] if out is not null;
 // the first copy of h clears h in `next`.
-constexpr int kFoldUnroll = 4;
+constexpr int kFoldUnroll = 2;
 template <int D, int U = kFoldUnroll>
 __device__ __forceinline__ void fold_copies(const FluxArgs& a, const float* x_in, float* x_out,
                                             float* out, const float* prev, float* next, int64_t i0,
