@@ -367,9 +367,15 @@ int ep_batch(ep_schedule *const *parts, int32_t count, ep_schedule **out);
 int ep_timing(ep_schedule *s, int32_t enable);
 int ep_timing_read(ep_schedule *s, int32_t kernel_class, double *total_ms, int64_t *launches);
 
-/* Threads that compute per CUDA block in the edge kernels (32..1024, multiple
- * of 32; default 192).  Does not change results beyond FP32 rounding order. */
+/* No counterpart in the paper (launch tuning): threads that compute per CUDA
+ * block in the forward flux and SpMV kernels (32..1024, multiple of 32;
+ * default 192), and in the adjoint flux kernels (default 352: the adjoint
+ * stages twice the state per kernel block and does about twice the arithmetic
+ * per task, so fewer CUDA blocks fit an SM and each wants more warps).
+ * EP_EINVAL for a count out of range.  Does not change results beyond FP32
+ * rounding order. */
 int ep_set_threads(ep_schedule *s, int32_t threads);
+int ep_set_adjoint_threads(ep_schedule *s, int32_t threads);
 
 /*
  * Edge-kernel organisation for flux steps (the software cache of Section 4).
@@ -377,7 +383,8 @@ int ep_set_threads(ep_schedule *s, int32_t threads);
  * stages = 2..8 (default 3): persistent CUDA blocks; a producer thread fills a
  * ring of that many shared-memory stages with 1-D TMA bulk copies of each
  * kernel block's contiguous pieces (its record run, slots, weights, shared
- * ids); consumer warps (ep_set_threads, at most 992 of them are used) take
+ * ids); consumer warps (ep_set_threads / ep_set_adjoint_threads, at most
+ * 928 threads of them are used beside the producer and fix-up warps) take
  * whole slices of 32 positions and compute one stage while the next ones
  * load.  Results agree up to FP32 rounding order.  Fewer stages are used when
  * that many do not fit in shared memory; when two do not fit, launches use the

@@ -214,6 +214,10 @@ class Schedule:
     def set_threads(self, threads: int):
         check(lib().ep_set_threads(self._h, threads))
 
+    def set_adjoint_threads(self, threads: int):
+        """Threads that compute per CUDA block in the adjoint kernels (default 352)."""
+        check(lib().ep_set_adjoint_threads(self._h, threads))
+
     def set_pipeline(self, stages: int):
         """0: one CUDA block per kernel block; 2..8: persistent pipelined kernel
         with that many shared-memory stages."""

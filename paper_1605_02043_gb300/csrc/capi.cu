@@ -134,7 +134,8 @@ struct EventTimer final : ep::dev::Timer {
 struct ep_schedule {
   ep::HostSchedule h;
   int device = -1;  // device holding the uploaded copy, -1 before upload
-  int tpb = 192;
+  int tpb = 192;      // consumer threads of the forward and SpMV kernels
+  int tpb_adj = 352;  // consumer threads of the adjoint kernels
   bool bacc_dirty = true;
   // device copy of the schedule
   DBuf d_desc, d_flist, d_ylist, d_ent, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
@@ -307,7 +308,7 @@ ep::dev::FluxArgs flux_args(ep_schedule* s, int kind, const float* w, const floa
   a.max_nslot = s->h.max_nslot;
   a.max_nsh = s->h.max_nsh;
   a.max_nsl = s->h.max_nsl;
-  a.tpb = s->tpb;
+  a.tpb = kind == kAdj ? s->tpb_adj : s->tpb;
   a.timer = s->t();
   return a;
 }
@@ -317,7 +318,7 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
 // Stage layout and grid of the pipelined kernels for state width D (cached;
 // recomputed when the stage count, thread count or stall hook changes).
 int tma_plan(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& P) {
-  const int key = 1 + s->stages + 16 * s->tpb + (1 << 16) * (s->stall + 1);
+  const int key = 1 + s->stages + 16 * (adjoint ? s->tpb_adj : s->tpb) + (1 << 16) * (s->stall + 1);
   if (s->plan_key[D][adjoint] != key) {
     if (int rc = tma_plan_compute(s, D, adjoint, s->plans[D][adjoint])) return rc;
     s->plan_key[D][adjoint] = key;
@@ -346,7 +347,8 @@ int tma_plan_compute(ep_schedule* s, int32_t D, bool adjoint, ep::dev::TmaPlan& 
   if (!P.fits) return EP_OK;  // the launch falls back to one CUDA block per schedule block
   P.smem = (size_t)L.stages * L.stage_bytes;
   // producer warp, fix-up warps, consumer warps
-  P.threads = 32 * (1 + ep::dev::kFixupWarps) + std::min(s->tpb, 1024 - 32 * (1 + ep::dev::kFixupWarps));
+  const int tpb = adjoint ? s->tpb_adj : s->tpb;
+  P.threads = 32 * (1 + ep::dev::kFixupWarps) + std::min(tpb, 1024 - 32 * (1 + ep::dev::kFixupWarps));
   const void* kern = ep::dev::flux_tma_kernel_ptr(D, adjoint);
   // the limit is a per-kernel attribute shared by every schedule: open it to
   // the device maximum (the launch still asks for P.smem)
@@ -1332,6 +1334,13 @@ int ep_set_threads(ep_schedule* s, int32_t threads) {
   if (!s) return fail(EP_EINVAL, "null schedule");
   if (threads < 32 || threads > 1024 || threads % 32) return fail(EP_EINVAL, "threads = %d", threads);
   s->tpb = threads;
+  return EP_OK;
+}
+
+int ep_set_adjoint_threads(ep_schedule* s, int32_t threads) {
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (threads < 32 || threads > 1024 || threads % 32) return fail(EP_EINVAL, "threads = %d", threads);
+  s->tpb_adj = threads;
   return EP_OK;
 }
 

@@ -132,6 +132,13 @@ def test_invalid_arguments():
             S.set_cache(bad)
     S.set_cache(E.CACHE_L1)
     S.set_cache(E.CACHE_SMEM)
+    for setter in (S.set_threads, S.set_adjoint_threads):
+        for bad in (0, 16, 48 + 1, 1056):
+            with pytest.raises(E.EpError) as ei:
+                setter(bad)
+            assert ei.value.code == -1
+        setter(32)
+        setter(1024)
     # blocks of more than 4096 vertex positions are too large for the L1 variant
     s2, d2 = W.knn_mesh(20000, 4, 0)
     big = E.Schedule.partition(s2, d2, 20000, 4000, default_order=True)
