@@ -77,7 +77,7 @@ def parse():
                     help="mesh: 1M-node kNN mesh flux steps (with the sub-records); rmat: R-MAT "
                          "scale-20 SpMV alone; batch: 512 uneven meshes alone")
     ap.add_argument("--meshes", type=int, default=512, help="batch workload: number of meshes")
-    ap.add_argument("--study", default="", choices=["", "cache"],
+    ap.add_argument("--study", default="", choices=["", "cache", "autotune"],
                     help="cache: shared-memory staging vs read-only data cache, C in {256, 512, 1024}, "
                          "partitioned and default schedules (one JSON line, no bench line)")
     return ap.parse_args()
@@ -495,7 +495,8 @@ def rmat_record(torch, E, args, ws, flush, C=512, cpu_seconds=5.0):
         alg = 8 * m + 64 * sch.k + 4 * cut + 4 * loads
         res[name] = dict(edge_updates_per_s=ws * m * len(ms) / (1e-3 * tot), ms_per_step=tot / len(ms),
                          kernel_ms=kms, loads=loads, vertex_cut=cut, alg_bytes=alg,
-                         roofline=roofline(alg, kms, "spmv_kernel", peak, peak_kind))
+                         roofline=roofline(alg, kms, "spmv_kernel", peak, peak_kind,
+                                           traffic(f"spmv_{sch.origin}_C{sch.C}_n{n}")))
     # the oracle on the host, bounded
     t0 = time.perf_counter()
     reps = 0
@@ -688,9 +689,42 @@ def batch_record(torch, E, args, ws, T=100, every=10, cpu_seconds=5.0):
     }
 
 
+def study_autotune(torch, E, args):
+    """The autotuner's pick against a full-batch sweep of every candidate
+    (every C in DEFAULT_CS x every (stages, threads) in DEFAULT_KERNELS, timed
+    the way the autotuner times them: one forward and one adjoint step, L2
+    flushed before each of 20 repetitions)."""
+    import workloads as W
+    from paper_1605_02043_gb300 import autotune
+
+    graphs = W.batch_meshes(args.meshes)
+    parts_by_C = {}
+    tuned = autotune.tune(graphs, D=D, partitions=parts_by_C, cache=None)
+    flush = autotune._Flush(torch)
+    full = []
+    for C in autotune.DEFAULT_CS:
+        parts = parts_by_C.get(C) or autotune.partition_many(graphs, C)
+        B = E.Schedule.batch(parts)
+        for (st, th), ms in zip(autotune.DEFAULT_KERNELS,
+                                autotune._time_configs(torch, B, D, autotune.DEFAULT_KERNELS, 20, TAU, flush)):
+            full.append(dict(C=C, stages=st, threads=th, ms=ms))
+        B.close()
+    best = min(full, key=lambda r: r["ms"])
+    pick = next(r for r in full if (r["C"], r["stages"], r["threads"]) ==
+                (tuned["C"], tuned["stages"], tuned["threads"]))
+    print(json.dumps({"study": "autotune", "meshes": args.meshes, "tuned": {k: tuned[k] for k in
+                      ("C", "stages", "threads")}, "screening": tuned["table"], "confirmed": tuned["confirmed"],
+                      "sample": tuned["sample"], "full_sweep": full, "best": best,
+                      "pick_over_best": pick["ms"] / best["ms"]}))
+
+
 def bench_batch(args):
     import torch
     import paper_1605_02043_gb300 as E
+
+    if args.study == "autotune":
+        study_autotune(torch, E, args)
+        return
 
     ws, rank, local = dist_info()
     if ws > 1:
