@@ -378,6 +378,30 @@ int ep_set_threads(ep_schedule *s, int32_t threads);
 int ep_set_adjoint_threads(ep_schedule *s, int32_t threads);
 
 /*
+ * No counterpart in the paper (multi-GPU sharding; the exchange volume is
+ * bounded by the auxiliary-edge cut of Section 3, Theorem 1).  A schedule of
+ * one shard (a contiguous range of another schedule's blocks) declares its
+ * halo: the nh data vertices (ids in [0, nd); any order, duplicates allowed)
+ * that other shards' tasks touch too.  Every halo vertex the shard touches
+ * then takes the shared-vertex path of the flux layout, so its per-step sum
+ * sits in an accumulator record instead of being applied in place.  Rebuilds
+ * the flux layout (the schedule, its vertex lists and its cost are
+ * unchanged), clears any pending state, and uploads again on the next call.
+ * EP_EINVAL for a bipartite schedule or an id out of range.
+ *
+ * ep_halo_pack: after ep_step_pending, copies the sums of the last forward
+ * edge kernel at the halo vertices into buf (device, nh x D floats, row i =
+ * halo vertex i, zeros where this shard does not touch it).  ep_halo_unpack
+ * writes buf back into those sums; between the two the caller sums buf over
+ * all shards (an all-reduce across processes, or a sum of the shards'
+ * buffers on one device).  The next step or ep_finish then applies the global
+ * sums to every copy.  Both are no-ops without a halo; enqueued on `stream`.
+ */
+int ep_set_halo(ep_schedule *s, const int32_t *halo, int64_t nh);
+int ep_halo_pack(ep_schedule *s, int32_t D, float *buf, void *stream);
+int ep_halo_unpack(ep_schedule *s, int32_t D, const float *buf, void *stream);
+
+/*
  * Edge-kernel organisation for flux steps (the software cache of Section 4).
  * stages = 0: one CUDA block per kernel block (stage, compute, write back).
  * stages = 2..8 (default 3): persistent CUDA blocks; a producer thread fills a

@@ -291,6 +291,22 @@ class Schedule:
         """Brings the shared copies of a pending state up to date (ep_finish)."""
         check(lib().ep_finish(self._h, D, _vp(x_lay), tau, _stream(stream)))
 
+    # ------------------------------------------------------------ shard halo
+    def set_halo(self, ids):
+        """Declares the data vertices other shards touch too (ep_set_halo); rebuilds
+        the flux layout.  halo_pack / halo_unpack then move their per-step sums."""
+        ids = np.ascontiguousarray(ids, np.int32)
+        self._halo_n = int(ids.size)
+        check(lib().ep_set_halo(self._h, ctypes.c_void_p(ids.ctypes.data), ids.size))
+
+    def halo_pack(self, D: int, buf, stream=None):
+        """Sums of the last forward step at the halo vertices into buf (nh x D, device)."""
+        check(lib().ep_halo_pack(self._h, D, _vp(buf), _stream(stream)))
+
+    def halo_unpack(self, D: int, buf, stream=None):
+        """buf (the sums over all shards) back into this shard's halo sums."""
+        check(lib().ep_halo_unpack(self._h, D, _vp(buf), _stream(stream)))
+
     def spmv_x_in(self, x, x_lay, stream=None):
         check(lib().ep_spmv_x_in(self._h, _vp(x), _vp(x_lay), _stream(stream)))
 

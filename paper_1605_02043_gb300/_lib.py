@@ -56,6 +56,9 @@ SIGNATURES = {
     "ep_timing_read": (ctypes.c_int, [P, I32, P, P]),
     "ep_set_threads": (ctypes.c_int, [P, I32]),
     "ep_set_adjoint_threads": (ctypes.c_int, [P, I32]),
+    "ep_set_halo": (ctypes.c_int, [P, P, I64]),
+    "ep_halo_pack": (ctypes.c_int, [P, I32, P, P]),
+    "ep_halo_unpack": (ctypes.c_int, [P, I32, P, P]),
     "ep_set_pipeline": (ctypes.c_int, [P, I32]),
     "ep_pipeline_info": (ctypes.c_int, [P, I32, I32, P, P, P, P, P]),
     "ep_check_errors": (ctypes.c_int, [P, P, P]),

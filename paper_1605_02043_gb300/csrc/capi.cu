@@ -148,6 +148,9 @@ struct ep_schedule {
   // records of every vertex (CSR) and the weight slots of every task (2 each)
   DBuf d_hptr, d_hrec, d_tslot;
   bool host_maps = false;
+  // shard halo (ep_set_halo): shared id of every halo vertex here, -1 if untouched
+  std::vector<int32_t> hmap;
+  DBuf d_hmap;
   const void* zeroed_x = nullptr;  // workspace buffers last cleared whole (their
   const void* zeroed_w = nullptr;  // padding is never written by the scatter kernels)
   EventTimer timer;
@@ -227,6 +230,7 @@ int ensure_device(ep_schedule* s) {
     CU(upload(s->d_gslot, h.gslot));
     CU(upload(s->d_wmap, h.wmap));
     CU(upload(s->d_rec, h.rec_of));
+    if (!s->hmap.empty()) CU(upload(s->d_hmap, s->hmap));
   }
   s->device = dev;
   return EP_OK;
@@ -1335,6 +1339,56 @@ int ep_set_threads(ep_schedule* s, int32_t threads) {
   if (threads < 32 || threads > 1024 || threads % 32) return fail(EP_EINVAL, "threads = %d", threads);
   s->tpb = threads;
   return EP_OK;
+}
+
+int ep_set_halo(ep_schedule* s, const int32_t* halo, int64_t nh) {
+  g_error.clear();
+  if (!s) return fail(EP_EINVAL, "null schedule");
+  if (bipartite(s)) return fail(EP_EINVAL, "a halo applies to flux schedules only");
+  if (nh < 0 || (nh > 0 && !halo)) return fail(EP_EINVAL, "null or negative halo list");
+  ep::HostSchedule& h = s->h;
+  for (int64_t i = 0; i < nh; ++i)
+    if (halo[i] < 0 || halo[i] >= h.nd) return fail(EP_EINVAL, "halo vertex %d out of range", halo[i]);
+  h.halo.assign(halo, halo + nh);
+  const std::string err = ep::rebuild_flux_layout(h);
+  if (!err.empty()) return fail(EP_EINVAL, "%s", err.c_str());
+  // shared id of every shared vertex's data vertex, then of every halo vertex
+  std::vector<int32_t> sid_of(h.nd, -1);
+  for (int64_t sh = 0; sh < h.n_sh; ++sh) sid_of[h.vrec[h.crec[h.cptr[sh]]]] = (int32_t)sh;
+  s->hmap.resize(nh);
+  for (int64_t i = 0; i < nh; ++i) s->hmap[i] = sid_of[halo[i]];
+  // the layout changed: upload again, new plans, new accumulators, new maps
+  s->device = -1;
+  for (auto& row : s->plan_key)
+    for (int& k : row) k = 0;
+  s->pending[0] = s->pending[1] = false;
+  s->bacc_dirty = true;
+  s->host_maps = false;
+  s->zeroed_x = s->zeroed_w = nullptr;
+  return EP_OK;
+}
+
+namespace {
+int halo_move_entry(ep_schedule* s, int32_t D, float* buf, bool pack, void* stream) {
+  g_error.clear();
+  if (int rc = check_flux(s, D)) return rc;
+  if (s->hmap.empty()) return EP_OK;
+  if (!buf) return fail(EP_EINVAL, "null buffer");
+  if (int rc = ensure_device(s)) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (int rc = ensure_bacc(s, D, st)) return rc;
+  ep::dev::FluxArgs a = flux_args(s, kFwd, nullptr, nullptr, nullptr, nullptr, 0.f);
+  CU(ep::dev::halo_move(a, D, s->d_hmap.as<int32_t>(), (int64_t)s->hmap.size(), buf, pack, st));
+  return EP_OK;
+}
+}  // namespace
+
+int ep_halo_pack(ep_schedule* s, int32_t D, float* buf, void* stream) {
+  return halo_move_entry(s, D, buf, true, stream);
+}
+
+int ep_halo_unpack(ep_schedule* s, int32_t D, const float* buf, void* stream) {
+  return halo_move_entry(s, D, const_cast<float*>(buf), false, stream);
 }
 
 int ep_set_adjoint_threads(ep_schedule* s, int32_t threads) {

@@ -120,6 +120,14 @@ __device__ __forceinline__ void acc_load(const float* bacc, int64_t h, float* v)
   }
 }
 template <int D, int K = 0>
+__device__ __forceinline__ void acc_store(float* bacc, int64_t h, const float* v) {
+  if constexpr (K < Planes<D>::NP) {
+    constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);
+    vst<W>(bacc + h * acc_stride(D) + F, v + F);
+    acc_store<D, K + 1>(bacc, h, v);
+  }
+}
+template <int D, int K = 0>
 __device__ __forceinline__ void acc_zero(float* bacc, int64_t h) {
   if constexpr (K < Planes<D>::NP) {
     constexpr int W = Planes<D>::width(K), F = Planes<D>::first(K);

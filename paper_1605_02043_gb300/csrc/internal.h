@@ -25,9 +25,9 @@ namespace ep {
 // warp reads one column with one access per array.  A slot holds the other
 // endpoint's position (bits 0-14) and a source flag (bit 15: this position is
 // the task's first endpoint), and the task weight in the same slot of the
-// weight layout; an unused slot has weight 0 and points at its own lane's
-// position (position 0 past the block's last position), so its term is exactly
-// zero.  Every task has one slot at each
+// weight layout; an unused slot has weight 0 and names some position of the
+// block (one that spreads the slice's loads over the shared-memory banks), so
+// its term is exactly zero.  Every task has one slot at each
 // endpoint (one for a self loop), so the forward flux is computed from either
 // side without signs (pull form).  Every per-block segment starts on a 16-byte
 // boundary and is padded to a multiple of 16 bytes (one bulk copy each).
@@ -103,6 +103,7 @@ struct HostSchedule {
   int32_t max_nv = 0, max_nslot = 0, max_nsh = 0, max_nsl = 0;
   int64_t w_pad = 0;           // slots of the weight layout
   std::vector<int32_t> wmap;   // weight slot -> task id (-1 for padding)
+  std::vector<int32_t> halo;   // data vertices forced onto the shared path (a shard's halo)
 
   // spmv layout (bipartite): x records 0..n-1, y records 0..n-1
   int64_t ny_int = 0, ny_bnd = 0;
@@ -135,6 +136,8 @@ bool partition_edges(const int32_t* src, const int32_t* dst, int64_t m, int64_t 
 // schedule.cpp: everything after the partition (Definition 4, vertex lists,
 // cpack, cost, kernel layout).  Returns an empty string or an error message.
 std::string build_schedule(HostSchedule& s, int threads);
+// The flux layout again (after `halo` changed); non-bipartite schedules only.
+std::string rebuild_flux_layout(HostSchedule& s);
 
 // State layout: the D components of a record are split into planes of
 // width 4, 2 and 1 (D = 4a + 2b + c); plane k holds n_rec records of its

@@ -363,6 +363,35 @@ __global__ void __launch_bounds__(kSpmvMaxThreads) spmv_kernel(const SpmvArgs a,
   spmv_write_out(d, a, ys, lane);
 }
 
+// ------------------------------------------------------------- shard halo
+
+// Halo sums of a shard schedule (one of several that split a schedule's
+// blocks): hmap[i] is the shared id of halo vertex i here, or -1 where this
+// shard does not touch it.  Pack copies the sums of the last forward edge
+// kernel (the accumulator buffer before the current phase) into buf[i][D]
+// (zeros for -1); unpack writes buf back after the sum over shards.
+template <int D>
+__global__ void halo_kernel(const FluxArgs a, const int32_t* __restrict__ hmap, int64_t nh,
+                            float* __restrict__ buf, bool pack) {
+  float* last = acc_buffer<D>(a, *a.phase + 2);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nh;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t h = __ldg(hmap + i);
+    float v[D];
+    if (pack) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) v[c] = 0.f;
+      if (h >= 0) acc_load<D>(last, h, v);
+#pragma unroll
+      for (int c = 0; c < D; ++c) buf[i * D + c] = v[c];
+    } else if (h >= 0) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) v[c] = buf[i * D + c];
+      acc_store<D>(last, h, v);
+    }
+  }
+}
+
 // ------------------------------------------------------------------- layout
 
 // caller layout [D][n] (by data vertex) <-> planar records (by record id)
@@ -736,6 +765,16 @@ cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, co
 #define EP_LIN(DD) layout_in_kernel<DD><<<g, 256, 0, st>>>(rec_of, n, n_rec, x, x_lay)
   EP_DISPATCH_D(D, EP_LIN)
 #undef EP_LIN
+  return cudaGetLastError();
+}
+
+cudaError_t halo_move(const FluxArgs& a, int D, const int32_t* hmap, int64_t nh, float* buf, bool pack,
+                      cudaStream_t st) {
+  if (nh <= 0) return cudaSuccess;
+  const int g = grid_for(nh, 256);
+#define EP_HALO(DD) halo_kernel<DD><<<g, 256, 0, st>>>(a, hmap, nh, buf, pack)
+  EP_DISPATCH_D(D, EP_HALO)
+#undef EP_HALO
   return cudaGetLastError();
 }
 

@@ -126,6 +126,11 @@ cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, co
                       float* x_lay, cudaStream_t st, Timer* t);
 cudaError_t layout_out(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x_lay,
                        float* x, cudaStream_t st, Timer* t);
+// halo sums of a shard schedule (forward kind): pack the last edge kernel's
+// sums of halo vertices i (shared id hmap[i], -1: not here) into buf[i][D], or
+// unpack buf into them
+cudaError_t halo_move(const FluxArgs& a, int D, const int32_t* hmap, int64_t nh, float* buf, bool pack,
+                      cudaStream_t st);
 // vertex-ordered forms, for inputs the GPU reads from host memory: x plane by
 // plane in vertex order into every record of each vertex (CSR ptr/recs), and
 // w in task order into the task's two slots (slots[2 t], slots[2 t + 1], -1

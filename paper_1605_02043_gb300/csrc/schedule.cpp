@@ -187,6 +187,11 @@ void place_slice(HostSchedule& s, const FluxDesc& d, int32_t j, const std::vecto
 std::string flux_layout_blocks(HostSchedule& s) {
   std::vector<int32_t> p, owner;
   usage(s, p, owner);
+  // halo vertices of a shard (touched by other shards' tasks too) take the
+  // shared path even when one block here uses them: their sums must go
+  // through an accumulator that the exchange can reach
+  for (int32_t v : s.halo)
+    if (v >= 0 && v < s.nd && p[v] == 1) p[v] = 2;
   auto align4 = [](int64_t v) { return (v + 3) & ~(int64_t)3; };
   auto pad_to = [](auto& v, size_t mult, auto fill) {
     while (v.size() % mult) v.push_back(fill);
@@ -527,6 +532,8 @@ std::string spmv_layout(HostSchedule& s) {
 }
 
 }  // namespace
+
+std::string rebuild_flux_layout(HostSchedule& s) { return flux_layout(s); }
 
 std::string build_schedule(HostSchedule& s, int threads) {
   if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());

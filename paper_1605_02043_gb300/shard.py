@@ -85,3 +85,97 @@ class Halo:
     def bytes_per_step(self, D: int) -> int:
         """Halo values one all-reduce moves per rank (4 D bytes per halo vertex)."""
         return 4 * D * int(self.ids.size)
+
+
+class ShardedFlux:
+    """Explicit flux steps of one schedule split over shards, on GPUs.
+
+    Shard g is the default-order schedule of its slice of the task order (it
+    reproduces blocks [lo_g, hi_g) exactly) with the halo declared
+    (`Schedule.set_halo`), so the sums of halo vertices stay in accumulator
+    records.  One step: every shard runs its edge kernel (one launch, shared
+    copies pending), packs its halo sums into a D x |halo| buffer, the buffers
+    are summed over shards by `reduce`, and every shard unpacks the global
+    sums, which its next step (or `finish`) applies to its copies.
+
+    `shards` lists the shard ids this process runs (all of them on one device,
+    or one per process); `reduce(bufs)` sums the listed shards' buffers over
+    every shard in place: the default sums them on the device (one process
+    holds every shard), across processes it is an all-reduce of the local sum.
+    """
+
+    def __init__(self, sched, src, dst, n: int, D: int, G: int, shards=None, reduce=None):
+        import torch
+        from . import Schedule
+
+        self.D, self.n, self.G = D, n, G
+        self.halo = Halo(sched.arrays(), G)
+        self.mine = list(range(G)) if shards is None else list(shards)
+        self.reduce = reduce or _sum_on_device
+        self.S, self.tasks = [], []
+        for g in self.mine:
+            s_, d_, t = self.halo.edges(g, src, dst)
+            S = Schedule.partition(s_, d_, n, sched.C, default_order=True)
+            S.set_halo(self.halo.ids)
+            self.S.append(S)
+            self.tasks.append(torch.as_tensor(t, dtype=torch.int64, device="cuda"))
+        f32 = dict(device="cuda", dtype=torch.float32)
+        self.xl = [torch.zeros(S.layout_floats(D), **f32) for S in self.S]
+        self.wl = [torch.zeros(S.weights_floats(), **f32) for S in self.S]
+        self.buf = [torch.zeros(self.halo.ids.size, D, **f32) for _ in self.S]
+
+    def load(self, x, w):
+        """Global state x (D x n) and task weights w (m), device tensors."""
+        for S, xl, wl, t in zip(self.S, self.xl, self.wl, self.tasks):
+            S.layout_in(x.contiguous(), xl)
+            S.weights_in(w.index_select(0, t).contiguous(), wl)
+
+    def step(self, tau: float = 1e-3):
+        for S, xl, wl, buf in zip(self.S, self.xl, self.wl, self.buf):
+            S.step(self.D, xl, xl, wl, None, tau, pending=True)
+            S.halo_pack(self.D, buf)
+        self.reduce(self.buf)
+        for S, buf in zip(self.S, self.buf):
+            S.halo_unpack(self.D, buf)
+
+    def finish(self, tau: float = 1e-3):
+        for S, xl in zip(self.S, self.xl):
+            S.finish(self.D, xl, tau)
+
+    def gather(self, x):
+        """Writes the vertices of this process's shards into x (D x n, device)."""
+        import torch
+
+        tmp = torch.empty_like(x)
+        for g, S, xl in zip(self.mine, self.S, self.xl):
+            S.layout_out(xl, tmp)
+            v = torch.as_tensor(self.halo.verts[g], dtype=torch.int64, device=x.device)
+            x.index_copy_(1, v, tmp.index_select(1, v))
+        return x
+
+
+def allreduce_sum(group=None):
+    """`reduce` for one process per GPU (or several shards per process): the
+    local buffers are summed, one all-reduce sums over processes, and every
+    local buffer takes the result."""
+    import torch.distributed as dist
+
+    def reduce(bufs):
+        total = bufs[0].clone()
+        for b in bufs[1:]:
+            total += b
+        dist.all_reduce(total, op=dist.ReduceOp.SUM, group=group)
+        for b in bufs:
+            b.copy_(total)
+
+    return reduce
+
+
+def _sum_on_device(bufs):
+    """Every shard on this device: each buffer becomes the sum of all of them."""
+    total = bufs[0].clone()
+    for b in bufs[1:]:
+        total += b
+    for b in bufs:
+        b.copy_(total)
+

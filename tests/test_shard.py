@@ -154,3 +154,63 @@ def test_halo_exchange_with_gloo_ranks(world):
     assert sum(c for _, _, c in res) >= n  # the shards cover every vertex
     for _, err, _ in res:
         assert err <= 1e-12
+
+
+def _reduce_main(rank, world, port, q):
+    import torch.distributed as dist
+    from paper_1605_02043_gb300.shard import allreduce_sum
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # two shards per rank: buffers rank * 10 + j
+        bufs = [torch.full((3, 5), float(rank * 10 + j)) for j in range(2)]
+        allreduce_sum()(bufs)
+        q.put((rank, [float(b[0, 0]) for b in bufs], [float(b.sum()) for b in bufs]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_allreduce_sum_of_shard_buffers():
+    """The multi-process exchange: every local buffer ends as the sum over all shards."""
+    import torch.multiprocessing as mp
+
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_reduce_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    want = float(sum(r * 10 + j for r in range(world) for j in range(2)))  # 0 + 1 + 10 + 11
+    for _, firsts, sums in res:
+        assert firsts == [want, want] and sums == [15 * want, 15 * want]
+
+
+def test_set_halo_keeps_the_schedule():
+    """ep_set_halo rebuilds only the flux layout: schedule arrays and cost stay."""
+    import paper_1605_02043_gb300 as E
+
+    src, dst = W.knn_mesh(4096, 4, 0)
+    S = E.Schedule.partition(src, dst, 4096, 256)
+    before = S.arrays()
+    cost = S.cost_host()
+    S.set_halo(np.array([0, 17, 17, 4095], np.int32))
+    after = S.arrays()
+    for key in ("block_ptr", "edge_perm", "vert_ptr", "vert_list", "relabel"):
+        assert np.array_equal(before[key], after[key]), key
+    assert S.cost_host() == cost
+    S.set_halo(np.array([], np.int32))
+    for bad in ([-1], [4096]):
+        with pytest.raises(E.EpError) as ei:
+            S.set_halo(np.array(bad, np.int32))
+        assert ei.value.code == -1
+    r, c = W.rmat(scale=10, m_draws=1 << 12, seed=1)
+    B = E.Schedule.partition(r, c, 1 << 10, 64, bipartite=True)
+    with pytest.raises(E.EpError):
+        B.set_halo(np.array([0], np.int32))
+
