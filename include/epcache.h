@@ -20,7 +20,7 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream); device work is enqueued on it and the call returns without
  *     synchronising unless stated otherwise.  The edge kernels and the
- *     shared-vertex fold are launched with programmatic stream
+ *     finish of pending shared copies are launched with programmatic stream
  *     serialisation and wait for the preceding kernel's completion before
  *     touching memory; a caller kernel placed just before them that signals
  *     its dependents early (griddepcontrol.launch_dependents) must have

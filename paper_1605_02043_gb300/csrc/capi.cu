@@ -403,7 +403,6 @@ int ensure_bacc(ep_schedule* s, int32_t D, cudaStream_t st) {
   return EP_OK;
 }
 
-// One forward step (edge kernel + shared-vertex fold) in schedule layout.
 // The one-block kernels stage a whole schedule block in shared memory.
 int block_fits(ep_schedule* s, size_t need) {
   int dev = 0, optin = 0;

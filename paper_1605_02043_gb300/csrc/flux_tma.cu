@@ -12,12 +12,16 @@
 //                  replicated in each block that uses it, a block's vertex set
 //                  is one run of records, so a stage fills in one round trip
 //                  with no dependent gather;
+//   fix-up warps   bring the staged copies of shared vertices up to date
+//                  with the previous step's sums (the copies lag one step)
+//                  and mark the stage "ready";
 //   consumer warps each take whole slices (32 positions) of a stage, sum the
 //                  flux of every position from shared memory (pull form),
-//                  write back (interior vertices in place, shared vertices with
-//                  one vector reduction into their accumulator, which the
-//                  fold kernel launched next applies to every copy), and
-//                  arrive on the stage's "empty" mbarrier.  Warps move through the
+//                  write back (interior vertices in place; shared vertices
+//                  one vector reduction into this step's accumulator, which
+//                  the next step or the finish applies to every copy, and
+//                  the up-to-date copy), and arrive on the stage's "empty"
+//                  mbarrier.  Warps move through the
 //                  stages independently (no block-wide barrier per kernel
 //                  block); slices are dealt so that every warp gets the same
 //                  share over the run.

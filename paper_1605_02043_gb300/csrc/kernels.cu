@@ -6,7 +6,9 @@
 // from HBM into shared memory, runs its tasks out of shared memory, and
 // writes back once per vertex: vertices no other block uses are updated in
 // place with plain stores, shared vertices get one vector atomic add into an
-// accumulator that a second, streaming kernel folds into the state.
+// accumulator, applied to every copy by the next step's fix-up or by the
+// finish (bnd_update_kernel).  Also here: the SpMV kernel, the cost kernels,
+// the layout conversions and the shard-halo moves.
 #include <cuda_runtime.h>
 
 #include <climits>
