@@ -310,9 +310,14 @@ int ep_finish(ep_schedule *s, int32_t D, float *x_lay, float tau, void *stream);
 /*
  * SpMV in schedule layout (bipartite schedules, Section 5.2): y_lay = A x_lay
  * with x_lay over column records and y_lay over row records (n floats each,
- * ep_spmv_x_in / ep_spmv_y_out permute), w_lay from ep_weights_in.  Rows
- * used by one block are stored, rows shared by blocks accumulated with
- * atomics after zeroing.  Buffers 16-byte aligned.
+ * ep_spmv_x_in / ep_spmv_y_out permute), w_lay from ep_weights_in.  One
+ * warp per schedule block: the block's x entries are staged in shared memory
+ * (the software cache), its row-ranked entries are split into equal chunks,
+ * one per lane, whatever the row lengths, and rows that cross chunk ends are
+ * joined by a segmented scan over the warp.  Rows used by one block are
+ * stored, rows shared by blocks accumulated with atomics after zeroing.
+ * Buffers 16-byte aligned (EP_EINVAL otherwise); EP_EINVAL when one warp's
+ * staged x and row totals of the largest block do not fit in shared memory.
  */
 int ep_spmv_x_in(ep_schedule *s, const float *x, float *x_lay, void *stream);
 int ep_spmv_y_out(ep_schedule *s, const float *y_lay, float *y, void *stream);
