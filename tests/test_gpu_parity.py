@@ -292,6 +292,22 @@ def test_run_host_matches_device(small_mesh):
     check_state(xh, xT, x0, 4, "x (pinned again)")
 
 
+@pytest.mark.parametrize("D", [1, 3, 8])
+def test_run_host_other_widths(small_mesh, D):
+    """The vertex-ordered host path for state widths with other plane splits."""
+    src, dst, n = small_mesh
+    S = E.Schedule.partition(src, dst, n, 512)
+    x0 = W.flux_state(n, D, 11)
+    w = W.flux_weights(src.size, 11)
+    xh = torch.from_numpy(np.array(x0, np.float32)).pin_memory()
+    wh = torch.from_numpy(np.array(w, np.float32)).pin_memory()
+    oh = torch.zeros_like(xh).pin_memory()
+    S.run_host(xh, wh, oh, steps=3, tau=1e-3, D=D)
+    xT, fT = O.flux_steps(src, dst, x0, w, 3, 1e-3)
+    check_state(xh, xT, x0, 3, f"x (D={D})")
+    check_field(oh, fT, f"out (D={D})")
+
+
 @pytest.mark.parametrize("pinned", [True, False])
 def test_run_host_spmv(pinned):
     n = 1 << 12
