@@ -140,7 +140,7 @@ struct ep_schedule {
   // device copy of the schedule
   DBuf d_desc, d_flist, d_ylist, d_ent, d_perm, d_wmap, d_rec, d_xrec, d_yrec, d_bptr, d_eu,
       d_ev;
-  DBuf d_sidx, d_soff, d_sid, d_vrec, d_gslot, d_frec, d_fsid;  // flux layout
+  DBuf d_sidx, d_soff, d_sid, d_gslot, d_frec, d_fsid;  // flux layout
   // workspace
   DBuf ws_x, ws_out, ws_w, ws_bacc, ws_lam, ws_gw, ws_hist, ws_flags, ws_cnt;
   DBuf ws_hx, ws_hw, ws_hout;
@@ -224,7 +224,6 @@ int ensure_device(ep_schedule* s) {
     CU(upload(s->d_sidx, h.sidx));
     CU(upload(s->d_soff, h.soff));
     CU(upload(s->d_sid, h.sid_list));
-    CU(upload(s->d_vrec, h.vrec));
     CU(upload(s->d_frec, h.fold_rec));
     CU(upload(s->d_fsid, h.fold_sid));
     CU(upload(s->d_gslot, h.gslot));
@@ -275,6 +274,18 @@ int ensure_host_maps(ep_schedule* s) {
   }
   CU(upload(s->d_tslot, tslot));
   s->host_maps = true;
+  return EP_OK;
+}
+
+// State from the caller's order into schedule layout: every vertex's values
+// are read once, in vertex order, and written to each of its records (a
+// gather by record would read each record's components from scattered
+// 4-byte locations).  Records of no vertex are left as they are: no kernel
+// reads them.
+int layout_in_state(ep_schedule* s, int32_t D, const float* x, float* x_lay, cudaStream_t st) {
+  if (int rc = ensure_host_maps(s)) return rc;
+  CU(ep::dev::layout_in_csr(s->d_hptr.as<int32_t>(), s->d_hrec.as<int32_t>(), s->h.nd, s->h.n_rec, D, x, x_lay,
+                            st, s->t()));
   return EP_OK;
 }
 
@@ -946,9 +957,7 @@ int ep_layout_in(ep_schedule* s, int32_t D, const float* x, float* x_lay, void* 
   if (misaligned(x_lay)) return fail(EP_EINVAL, "schedule-layout buffers must be 16-byte aligned");
   if (int rc = ensure_device(s)) return rc;
   fresh_state(s);
-  CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), s->h.nd, s->h.n_rec, D, x, x_lay,
-                        as_stream(stream), s->t()));
-  return EP_OK;
+  return layout_in_state(s, D, x, x_lay, as_stream(stream));
 }
 
 int ep_layout_out(ep_schedule* s, int32_t D, const float* x_lay, float* x, void* stream) {
@@ -1110,18 +1119,11 @@ int run_flux(ep_schedule* s, int32_t D, int32_t steps, float tau, float* x, cons
   }
   fresh_state(s);
   if (int rc = ensure_bacc(s, D, st)) return rc;
-  if (from_host) {
-    if (int rc = ensure_host_maps(s)) return rc;
-    if (s->zeroed_x != s->ws_x.p) {  // records of no vertex stay zero
-      CU(cudaMemsetAsync(s->ws_x.p, 0, s->ws_x.bytes, st));
-      s->zeroed_x = s->ws_x.p;
-    }
-    CU(ep::dev::layout_in_csr(s->d_hptr.as<int32_t>(), s->d_hrec.as<int32_t>(), h.nd, h.n_rec, D, x,
-                              s->ws_x.as<float>(), st, s->t()));
-  } else {
-    CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, x, s->ws_x.as<float>(), st, s->t()));
-    s->zeroed_x = nullptr;
+  if (s->zeroed_x != s->ws_x.p) {  // records of no vertex stay zero
+    CU(cudaMemsetAsync(s->ws_x.p, 0, s->ws_x.bytes, st));
+    s->zeroed_x = s->ws_x.p;
   }
+  if (int rc = layout_in_state(s, D, x, s->ws_x.as<float>(), st)) return rc;
   if (int rc = weights_to_ws(s, w, from_host, st)) return rc;
   if (out) CU(cudaMemsetAsync(s->ws_out.p, 0, lay, st));
   // the shared copies stay pending between steps; the last step finishes them
@@ -1204,7 +1206,7 @@ int ep_run_adjoint(ep_schedule* s, const float* x0, const float* w, float* lam, 
   fresh_state(s);
   if (int rc = ensure_bacc(s, D, st)) return rc;
   float* hist = s->ws_hist.as<float>();
-  CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, x0, hist, st, s->t()));
+  if (int rc = layout_in_state(s, D, x0, hist, st)) return rc;
   CU(ep::dev::gather(wmap_of(s), wlen_of(s), w, s->ws_w.as<float>(), st, s->t()));
   CU(cudaMemsetAsync(s->ws_gw.p, 0, (size_t)wlen_of(s) * sizeof(float), st));
   // the recomputed states are read whole by the adjoint: finish every one
@@ -1212,8 +1214,7 @@ int ep_run_adjoint(ep_schedule* s, const float* x0, const float* w, float* lam, 
     if (int rc = flux_step_any(s, D, s->ws_w.as<float>(), hist + lay * t, hist + lay * (t + 1), nullptr,
                                tau, true, st))
       return rc;
-  CU(ep::dev::layout_in_rec(s->d_vrec.as<int32_t>(), h.nd, h.n_rec, D, lam, s->ws_lam.as<float>(), st,
-                            s->t()));
+  if (int rc = layout_in_state(s, D, lam, s->ws_lam.as<float>(), st)) return rc;
   // the cotangent's shared copies stay pending between adjoint steps
   for (int32_t t = steps - 1; t >= 0; --t)
     if (int rc = flux_adj_any(s, D, s->ws_w.as<float>(), hist + lay * t, s->ws_lam.as<float>(),

@@ -409,24 +409,9 @@ __global__ void layout_in_kernel(const int32_t* __restrict__ rec_of, int64_t n, 
   }
 }
 
-// flux layout: every record r (block runs with their copies of shared
-// vertices, then the untouched vertices) <- its data vertex vrec[r]; padding
-// records get 0
-template <int D>
-__global__ void layout_in_rec_kernel(const int32_t* __restrict__ vrec, int64_t n, int64_t n_rec,
-                                     const float* __restrict__ x, float* __restrict__ x_lay) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rec;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = __ldg(vrec + r);
-    float t[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) t[c] = v >= 0 ? __ldg(x + (size_t)c * n + v) : 0.f;
-    rec_store<D>(x_lay, n_rec, r, t);
-  }
-}
-
-// x read in vertex order (coalesced, for x in host memory the GPU reads over
-// the host link), every record of vertex v written: recs[ptr[v] .. ptr[v + 1])
+// flux layout in: x read in vertex order (coalesced; in host memory the GPU
+// reads it over the host link), every record of vertex v written (its record
+// and the copies of a shared vertex): recs[ptr[v] .. ptr[v + 1])
 template <int D>
 __global__ void layout_in_csr_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ recs,
                                      int64_t n, int64_t n_rec, const float* __restrict__ x,
@@ -794,16 +779,6 @@ cudaError_t weights_scatter(const int32_t* slots, int64_t m, const float* w, flo
                             Timer* t) {
   Scope sc(t, T_LAYOUT, st);
   weights_scatter_kernel<<<grid_for(m, 256), 256, 0, st>>>(reinterpret_cast<const int2*>(slots), m, w, w_lay);
-  return cudaGetLastError();
-}
-
-cudaError_t layout_in_rec(const int32_t* vrec, int64_t n, int64_t n_rec, int D, const float* x,
-                          float* x_lay, cudaStream_t st, Timer* t) {
-  Scope sc(t, T_LAYOUT, st);
-  const int g = grid_for(n_rec, 256);
-#define EP_LIN(DD) layout_in_rec_kernel<DD><<<g, 256, 0, st>>>(vrec, n, n_rec, x, x_lay)
-  EP_DISPATCH_D(D, EP_LIN)
-#undef EP_LIN
   return cudaGetLastError();
 }
 

@@ -117,10 +117,6 @@ struct SpmvPlan {
   size_t smem;  // dynamic shared memory per CUDA block
 };
 SpmvPlan spmv_plan(const SpmvArgs& a, int smem_optin);
-// flux layout in: record r of x_lay <- x[.][vrec[r]] (0 where vrec[r] < 0), n data
-// vertices, state planes of n_rec records
-cudaError_t layout_in_rec(const int32_t* vrec, int64_t n, int64_t n_rec, int D, const float* x,
-                          float* x_lay, cudaStream_t st, Timer* t);
 // SpMV layout in (one record per vertex): x_lay[rec_of[v]] <- x[v]
 cudaError_t layout_in(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, const float* x,
                       float* x_lay, cudaStream_t st, Timer* t);
@@ -131,10 +127,10 @@ cudaError_t layout_out(const int32_t* rec_of, int64_t n, int64_t n_rec, int D, c
 // unpack buf into them
 cudaError_t halo_move(const FluxArgs& a, int D, const int32_t* hmap, int64_t nh, float* buf, bool pack,
                       cudaStream_t st);
-// vertex-ordered forms, for inputs the GPU reads from host memory: x plane by
-// plane in vertex order into every record of each vertex (CSR ptr/recs), and
-// w in task order into the task's two slots (slots[2 t], slots[2 t + 1], -1
-// for none)
+// vertex- and task-ordered input forms: x plane by plane in vertex order into
+// every record of each vertex (CSR ptr/recs; the flux layout in), and w in
+// task order into the task's two slots (slots[2 t], slots[2 t + 1], -1 for
+// none; for weights in host memory)
 cudaError_t layout_in_csr(const int32_t* ptr, const int32_t* recs, int64_t n, int64_t n_rec, int D,
                           const float* x, float* x_lay, cudaStream_t st, Timer* t);
 cudaError_t weights_scatter(const int32_t* slots, int64_t m, const float* w, float* w_lay, cudaStream_t st,
