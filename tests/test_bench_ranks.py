@@ -52,3 +52,27 @@ def test_max_over_ranks_with_gloo(world):
         assert (rank, ws, local) == (r, world, r)
         assert t == slowest
         assert value == pytest.approx(world * 1000 / (1e-3 * slowest))
+
+
+def test_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """The bench takes ncu traffic from profiles/traffic.json only while the
+    kernel sources hash to the recorded value."""
+    import json
+    import shutil
+
+    import bench
+
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(bench.ROOT, "paper_1605_02043_gb300", "csrc"),
+                    root / "paper_1605_02043_gb300" / "csrc")
+    (root / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    sha = bench.kernel_sources_sha()
+    rec = {"k": {"kernel_sources_sha": sha, "dram_bytes_per_launch": 123},
+           "old": {"kernel_sources_sha": "0" * 16, "dram_bytes_per_launch": 456}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.traffic("k") == 123
+    assert bench.traffic("old") is None and bench.traffic("missing") is None
+    with open(root / "paper_1605_02043_gb300" / "csrc" / "kernels.cu", "a") as fh:
+        fh.write("\n// changed\n")
+    assert bench.kernel_sources_sha() != sha and bench.traffic("k") is None
