@@ -4,7 +4,8 @@
   vertex lists, relabel and cost bit-exact with the oracle; 10 explicit steps
   and the 10-step adjoint, both through ep_run_adjoint and through the
   checkpointed autograd function (every 5 steps), against the FP64 oracle.
-* R-MAT scale 20, C = 512, bipartite: full SpMV against the FP64 oracle; the
+* R-MAT scale 20, C = 512, bipartite: full SpMV (staged x and read-only
+  cache) against the FP64 oracle; the
   schedule is checked through properties that hold at any size (exact block
   sizes, each task once, GPU cost = host cost = loads recomputed from the
   vertex lists); the oracle partition itself is too slow for this size.
@@ -121,9 +122,11 @@ def test_rmat20_spmv_and_schedule_properties():
     for dflt in (False, True):
         Sx = S if not dflt else E.Schedule.partition(rows, cols, n, 512, bipartite=True, default_order=True)
         Sx.set_threads(192)
-        y = torch.empty(n, device="cuda")
-        Sx.run(cuda(x0), cuda(w), y, kernel=E.SPMV)
-        check_field(y, ref, f"y default_order={dflt}")
+        for cache in (E.CACHE_SMEM, E.CACHE_L1):
+            Sx.set_cache(cache)
+            y = torch.empty(n, device="cuda")
+            Sx.run(cuda(x0), cuda(w), y, kernel=E.SPMV)
+            check_field(y, ref, f"y default_order={dflt} cache={cache}")
 
 
 def test_batch512_cuda_graph_fwd_bwd_autotuned():
